@@ -1,0 +1,505 @@
+/*
+ * llg_oracle.c -- plain, slow FP64 CPU oracle for the stochastic LLG hysteresis-loop path of
+ * Behbahani, Plumer & Saika-Voivod, "Coarse-graining in micromagnetic simulations of dynamic
+ * hysteresis loops" (arXiv:1912.00310).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes or calls this file;
+ * only the tests, the smoke check and the CPU-baseline leg of the benchmark load it.  It shares no
+ * code, header, table or constant generator with the CUDA path.
+ *
+ * What it computes, in the paper's order and notation:
+ *   - Eq. 1 (LLG in Landau-Lifshitz form): dM/dt = -g1 M x H_eff - (alpha g1/Ms) M x (M x H_eff),
+ *     g1 = mu0 ge / (1 + alpha^2), ge = 1.76e11 rad/(s T).  Written for the unit vector m = M/Ms.
+ *   - H_eff = exchange (6-neighbour cubic stencil) + uniaxial anisotropy along u + Zeeman field
+ *     along z + Brown thermal field (material paragraph; thermal-field paragraph after Eq. 1).
+ *   - Coarse-graining (Eqs. 8-13): zeta(b) = t/b + 1 - t, t = T/Tc; A(b) = zeta A0,
+ *     K(b) = zeta^3 K0; H0 = H(b)/zeta; M0 = zeta M(b) (Eq. 11) or the delta-corrected
+ *     M0 = delta zeta M(b) + (1 - delta) M(b) (Eq. 13).
+ *   - Loop observables: m_H = z component of the cell-averaged unit magnetisation, averaged over
+ *     independent realisations; coercive field with one standard error; loop area.
+ * Readings where the paper is silent (all listed in the design notes): thermal-field variance
+ * sigma^2 = 2 alpha kB T / (g0 mu0 Ms V dt) with g0 = mu0 ge; Heun predictor-corrector with
+ * renormalisation of predictor and corrector and one thermal draw per step; exchange field
+ * (2A/(mu0 Ms a^2)) sum_j m_j with free faces; Philox4x32-10 noise keyed by (seed, realisation)
+ * with counter (cell, step_lo, step_hi, 0) and Box-Muller on 24-bit uniforms.
+ *
+ * Precision: double throughout.  Parallelism: one POSIX thread per group of realisations
+ * (realisations are independent; results do not depend on the thread count).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+#define ORC_MU0 (4.0e-7 * ORC_PI)          /* vacuum permeability, T m / A            */
+#define ORC_GE 1.76e11                      /* electron gyromagnetic ratio, rad/(s T)  */
+#define ORC_KB 1.380649e-23                 /* Boltzmann constant, J/K                 */
+#define ORC_OE_TO_AM (1000.0 / (4.0 * ORC_PI)) /* 1 Oe in A/m                          */
+
+/* ------------------------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as easy as 1, 2, 3",   */
+/* SC'11).  A 4x32-bit counter is mixed with a 2x32-bit key by ten rounds; each round multiplies */
+/* counter words 0 and 2 by the two Philox multipliers, swaps the halves, xors in the key, and  */
+/* the key is advanced by the two Weyl constants between rounds.                                 */
+/* ------------------------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint32_t mult0 = 0xD2511F53u, mult1 = 0xCD9E8D57u;
+    const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += weyl0;
+            k1 += weyl1;
+        }
+        uint64_t prod0 = (uint64_t)mult0 * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)mult1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* Uniform in (0,1) from the top 24 bits of a 32-bit word: (floor(x / 256) + 1/2) / 2^24. */
+double orc_uniform24(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
+
+/* Three standard normals for (seed, realisation, cell, step): Box-Muller on the pairs
+ * (u0, u1) -> (n0, n1) and (u2, u3) -> n2 (the fourth normal is not used). */
+void orc_thermal_normals(uint32_t seed, uint32_t real, uint32_t cell, uint64_t step, double n[3])
+{
+    uint32_t ctr[4] = {cell, (uint32_t)step, (uint32_t)(step >> 32), 0u};
+    uint32_t key[2] = {seed, real};
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, key, x);
+    double u0 = orc_uniform24(x[0]), u1 = orc_uniform24(x[1]);
+    double u2 = orc_uniform24(x[2]), u3 = orc_uniform24(x[3]);
+    double r01 = sqrt(-2.0 * log(u0));
+    double r23 = sqrt(-2.0 * log(u2));
+    n[0] = r01 * cos(2.0 * ORC_PI * u1);
+    n[1] = r01 * sin(2.0 * ORC_PI * u1);
+    n[2] = r23 * cos(2.0 * ORC_PI * u3);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Coarse-graining map, Eqs. 8-13.                                                             */
+/* ------------------------------------------------------------------------------------------ */
+double orc_zeta(double b, double T, double Tc)
+{
+    double t = T / Tc;
+    return t / b + 1.0 - t;
+}
+
+/* Exchange length of the renormalised material, l_ex,b = sqrt(2 zeta A0 / (mu0 Ms^2)). */
+double orc_exchange_length(double zeta, double A0, double Ms)
+{
+    return sqrt(2.0 * zeta * A0 / (ORC_MU0 * Ms * Ms));
+}
+
+/* Factor that maps a simulated m_H at level b back to the unscaled system: Eq. 11 for
+ * mode 1 (zeta), Eq. 13 for mode 2 (delta zeta + 1 - delta); mode 0 leaves m unchanged. */
+double orc_m_rescale(int mode, double zeta, double delta)
+{
+    if (mode == 1) return zeta;
+    if (mode == 2) return delta * zeta + (1.0 - delta);
+    return 1.0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Problem description.  All quantities are the simulation-level values (already rescaled).    */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int nx, ny, nz;
+    unsigned periodic;   /* bit0 x, bit1 y, bit2 z */
+    double a;            /* cell edge, m                                  */
+    double volume;       /* cell volume, m^3 (a^3 for cubic cells)        */
+    double A;            /* exchange stiffness, J/m                       */
+    double K;            /* uniaxial anisotropy, J/m^3                    */
+    double Ms;           /* saturation magnetisation, A/m                 */
+    double alpha;        /* Gilbert damping                               */
+    double T;            /* temperature, K                                */
+    double u[3];         /* easy axis (unit vector)                       */
+    double dt;           /* time step, s                                  */
+    double H_start_Oe;   /* field at step 0                               */
+    double H_turn_Oe;    /* field at the turning point                    */
+    int64_t n_half;      /* steps from H_start to H_turn (0: constant)    */
+} orc_problem;
+
+typedef struct {
+    double g0, g1, ag1;  /* mu0 ge, g1 = g0/(1+alpha^2), alpha g1 */
+    double c_ex;         /* 2A / (mu0 Ms a^2), A/m                 */
+    double c_an;         /* 2K / (mu0 Ms), A/m                     */
+    double sigma;        /* thermal-field standard deviation, A/m  */
+} orc_coeffs;
+
+void orc_coefficients(const orc_problem *p, double out[6])
+{
+    double g0 = ORC_MU0 * ORC_GE;
+    out[0] = g0;
+    out[1] = g0 / (1.0 + p->alpha * p->alpha);
+    out[2] = p->alpha * out[1];
+    out[3] = 2.0 * p->A / (ORC_MU0 * p->Ms * p->a * p->a);
+    out[4] = 2.0 * p->K / (ORC_MU0 * p->Ms);
+    out[5] = (p->T > 0.0)
+                 ? sqrt(2.0 * p->alpha * ORC_KB * p->T / (g0 * ORC_MU0 * p->Ms * p->volume * p->dt))
+                 : 0.0;
+}
+
+static orc_coeffs coeffs_of(const orc_problem *p)
+{
+    double c[6];
+    orc_coefficients(p, c);
+    orc_coeffs r = {c[0], c[1], c[2], c[3], c[4], c[5]};
+    return r;
+}
+
+/* Zeeman field along z at step n, in Oe: a triangle wave from H_start to H_turn and back, with
+ * n_half steps per half period. */
+double orc_field_Oe(const orc_problem *p, int64_t n)
+{
+    if (p->n_half <= 0) return p->H_start_Oe;
+    int64_t period = 2 * p->n_half;
+    int64_t ph = n % period;
+    int64_t tri = ph <= p->n_half ? ph : period - ph;
+    return p->H_start_Oe + (p->H_turn_Oe - p->H_start_Oe) * ((double)tri / (double)p->n_half);
+}
+
+static int64_t ncells_of(const orc_problem *p) { return (int64_t)p->nx * p->ny * p->nz; }
+
+/* Effective field at cell (x,y,z) of state m (unit vectors), field Hz (A/m) along z, thermal
+ * field hth. */
+static void effective_field(const orc_problem *p, const orc_coeffs *c, const double *m, int x, int y,
+                            int z, double Hz, const double *hth, double H[3])
+{
+    double s[3] = {0.0, 0.0, 0.0};
+    const int dims[3] = {p->nx, p->ny, p->nz};
+    const int pos[3] = {x, y, z};
+    for (int axis = 0; axis < 3; ++axis) {
+        for (int dir = -1; dir <= 1; dir += 2) {
+            int q[3] = {pos[0], pos[1], pos[2]};
+            q[axis] += dir;
+            if (q[axis] < 0 || q[axis] >= dims[axis]) {
+                if (!(p->periodic & (1u << axis))) continue; /* free face: no neighbour */
+                q[axis] = (q[axis] + dims[axis]) % dims[axis];
+            }
+            int64_t j = q[0] + (int64_t)p->nx * (q[1] + (int64_t)p->ny * q[2]);
+            s[0] += m[3 * j + 0];
+            s[1] += m[3 * j + 1];
+            s[2] += m[3 * j + 2];
+        }
+    }
+    int64_t i = x + (int64_t)p->nx * (y + (int64_t)p->ny * z);
+    const double *mi = m + 3 * i;
+    double mu = mi[0] * p->u[0] + mi[1] * p->u[1] + mi[2] * p->u[2];
+    for (int k = 0; k < 3; ++k) H[k] = c->c_ex * s[k] + c->c_an * mu * p->u[k] + hth[k];
+    H[2] += Hz;
+}
+
+/* Right-hand side of Eq. 1 for the unit vector: f = -g1 m x H - alpha g1 m x (m x H). */
+static void llg_rhs(const orc_coeffs *c, const double m[3], const double H[3], double f[3])
+{
+    double mxH[3] = {m[1] * H[2] - m[2] * H[1], m[2] * H[0] - m[0] * H[2], m[0] * H[1] - m[1] * H[0]};
+    double mxmxH[3] = {m[1] * mxH[2] - m[2] * mxH[1], m[2] * mxH[0] - m[0] * mxH[2],
+                       m[0] * mxH[1] - m[1] * mxH[0]};
+    for (int k = 0; k < 3; ++k) f[k] = -c->g1 * mxH[k] - c->ag1 * mxmxH[k];
+}
+
+static void normalise(double v[3])
+{
+    double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= n;
+    v[1] /= n;
+    v[2] /= n;
+}
+
+typedef struct {
+    double *mt, *f0, *hth;
+} work_buffers;
+
+/* One Heun step n -> n+1 of one realisation, in place on m. */
+static void heun_step(const orc_problem *p, const orc_coeffs *c, uint32_t seed, uint32_t real,
+                      int64_t n, double *m, work_buffers *w)
+{
+    const int64_t N = ncells_of(p);
+    const double Hn = orc_field_Oe(p, n) * ORC_OE_TO_AM;
+    const double Hn1 = orc_field_Oe(p, n + 1) * ORC_OE_TO_AM;
+    /* thermal field, drawn once per step and used by both stages */
+    for (int64_t i = 0; i < N; ++i) {
+        double xi[3];
+        if (c->sigma > 0.0) {
+            orc_thermal_normals(seed, real, (uint32_t)i, (uint64_t)n, xi);
+        } else {
+            xi[0] = xi[1] = xi[2] = 0.0;
+        }
+        for (int k = 0; k < 3; ++k) w->hth[3 * i + k] = c->sigma * xi[k];
+    }
+    /* predictor: mt = normalise(m + dt f(m, t_n)) */
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                int64_t i = x + (int64_t)p->nx * (y + (int64_t)p->ny * z);
+                double H[3];
+                effective_field(p, c, m, x, y, z, Hn, w->hth + 3 * i, H);
+                llg_rhs(c, m + 3 * i, H, w->f0 + 3 * i);
+                for (int k = 0; k < 3; ++k) w->mt[3 * i + k] = m[3 * i + k] + p->dt * w->f0[3 * i + k];
+                normalise(w->mt + 3 * i);
+            }
+    /* corrector: m <- normalise(m + dt/2 (f(m, t_n) + f(mt, t_{n+1}))) */
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                int64_t i = x + (int64_t)p->nx * (y + (int64_t)p->ny * z);
+                double H[3], f1[3];
+                effective_field(p, c, w->mt, x, y, z, Hn1, w->hth + 3 * i, H);
+                llg_rhs(c, w->mt + 3 * i, H, f1);
+                for (int k = 0; k < 3; ++k)
+                    m[3 * i + k] = m[3 * i + k] + 0.5 * p->dt * (w->f0[3 * i + k] + f1[k]);
+                normalise(m + 3 * i);
+            }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Ensemble driver.                                                                            */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+    const orc_problem *p;
+    uint32_t seed;
+    int n_real;
+    uint32_t real0;
+    int64_t step0, n_steps;
+    double *m_state;     /* [n_real][N][3] */
+    int64_t sample_every;
+    int64_t n_samples;   /* columns of samples */
+    double *samples;     /* [n_real][n_samples], indexed by global sample number */
+    double *mz_timeavg;  /* [n_real] or NULL: mean of cell-averaged m_z over all steps after
+                            burn_in (state after each step) */
+    int64_t burn_in;
+    int next_real;
+    pthread_mutex_t lock;
+} run_job;
+
+static double mean_mz(const double *m, int64_t N)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < N; ++i) s += m[3 * i + 2];
+    return s / (double)N;
+}
+
+static void run_one(run_job *job, int r)
+{
+    const orc_problem *p = job->p;
+    const int64_t N = ncells_of(p);
+    orc_coeffs c = coeffs_of(p);
+    work_buffers w;
+    w.mt = (double *)malloc(sizeof(double) * 3 * N);
+    w.f0 = (double *)malloc(sizeof(double) * 3 * N);
+    w.hth = (double *)malloc(sizeof(double) * 3 * N);
+    double *m = job->m_state + (int64_t)r * N * 3;
+    double acc = 0.0;
+    int64_t acc_n = 0;
+    for (int64_t s = 0; s < job->n_steps; ++s) {
+        int64_t n = job->step0 + s;
+        heun_step(p, &c, job->seed, job->real0 + (uint32_t)r, n, m, &w);
+        int64_t done = n + 1;
+        if (job->samples && job->sample_every > 0 && done % job->sample_every == 0) {
+            int64_t k = done / job->sample_every;
+            if (k < job->n_samples) job->samples[(int64_t)r * job->n_samples + k] = mean_mz(m, N);
+        }
+        if (job->mz_timeavg && s >= job->burn_in) {
+            acc += mean_mz(m, N);
+            ++acc_n;
+        }
+    }
+    if (job->mz_timeavg) job->mz_timeavg[r] = acc_n ? acc / (double)acc_n : 0.0;
+    free(w.mt);
+    free(w.f0);
+    free(w.hth);
+}
+
+static void *run_worker(void *arg)
+{
+    run_job *job = (run_job *)arg;
+    for (;;) {
+        pthread_mutex_lock(&job->lock);
+        int r = job->next_real++;
+        pthread_mutex_unlock(&job->lock);
+        if (r >= job->n_real) break;
+        run_one(job, r);
+    }
+    return NULL;
+}
+
+/* Advance n_real realisations (keys (seed, real0 + r)) from step0 by n_steps Heun steps.
+ * m_state [n_real][nx*ny*nz][3] is updated in place.  If samples is given, the cell-averaged m_z
+ * after every step whose index (step0 + s + 1) is a multiple of sample_every is stored at column
+ * (step index / sample_every).  If mz_timeavg is given, it receives, per realisation, the mean
+ * of the cell-averaged m_z over the steps s >= burn_in of this call.  Returns 0. */
+int orc_run(const orc_problem *p, uint32_t seed, int n_real, uint32_t real0, int64_t step0,
+            int64_t n_steps, double *m_state, int64_t sample_every, int64_t n_samples,
+            double *samples, double *mz_timeavg, int64_t burn_in, int n_threads)
+{
+    run_job job;
+    job.p = p;
+    job.seed = seed;
+    job.n_real = n_real;
+    job.real0 = real0;
+    job.step0 = step0;
+    job.n_steps = n_steps;
+    job.m_state = m_state;
+    job.sample_every = sample_every;
+    job.n_samples = n_samples;
+    job.samples = samples;
+    job.mz_timeavg = mz_timeavg;
+    job.burn_in = burn_in;
+    job.next_real = 0;
+    pthread_mutex_init(&job.lock, NULL);
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > n_real) n_threads = n_real;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, run_worker, &job);
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&job.lock);
+    return 0;
+}
+
+/* Total energy (J) of a state at field H (Oe along z): exchange per nearest-neighbour pair
+ * 2 A a (1 - m_i . m_j), anisotropy -K V (m.u)^2, Zeeman -mu0 Ms V H m_z.  The effective field of
+ * Eq. 1 is -(1/(mu0 Ms V)) dE/dm_i of this energy. */
+double orc_energy(const orc_problem *p, const double *m, double H_Oe)
+{
+    const double H = H_Oe * ORC_OE_TO_AM;
+    double e = 0.0;
+    const int dims[3] = {p->nx, p->ny, p->nz};
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                int64_t i = x + (int64_t)p->nx * (y + (int64_t)p->ny * z);
+                const double *mi = m + 3 * i;
+                int pos[3] = {x, y, z};
+                for (int axis = 0; axis < 3; ++axis) { /* each pair once: the +1 neighbour */
+                    int q[3] = {pos[0], pos[1], pos[2]};
+                    q[axis] += 1;
+                    if (q[axis] >= dims[axis]) {
+                        if (!(p->periodic & (1u << axis))) continue; /* free face */
+                        q[axis] = 0; /* periodic: the wrapped bond is a bond of its own */
+                    }
+                    int64_t j = q[0] + (int64_t)p->nx * (q[1] + (int64_t)p->ny * q[2]);
+                    const double *mj = m + 3 * j;
+                    e += 2.0 * p->A * p->a * (1.0 - (mi[0] * mj[0] + mi[1] * mj[1] + mi[2] * mj[2]));
+                }
+                double mu = mi[0] * p->u[0] + mi[1] * p->u[1] + mi[2] * p->u[2];
+                e -= p->K * p->volume * mu * mu;
+                e -= ORC_MU0 * p->Ms * p->volume * H * mi[2];
+            }
+    return e;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Loop observables (sample spacing in field, mean loop over realisations).                   */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Coercive field of one mean loop m[0..n-1] at fields H[0..n-1], the loop starting at
+ * positive saturation and turning at sample k_turn: the first zero crossing after the start on
+ * the descending branch and the first after the turning point on the ascending branch, each by
+ * linear interpolation; Hc = (|Hc_down| + |Hc_up|) / 2.  Returns NAN when a branch has no
+ * crossing. */
+static double crossing(const double *H, const double *m, int64_t k0, int64_t k1, int descending)
+{
+    for (int64_t k = k0; k < k1; ++k) {
+        double a = m[k], b = m[k + 1];
+        int hit = descending ? (a > 0.0 && b <= 0.0) : (a < 0.0 && b >= 0.0);
+        if (hit) {
+            double f = a / (a - b);
+            return H[k] + f * (H[k + 1] - H[k]);
+        }
+    }
+    return NAN;
+}
+
+double orc_coercive_field(const double *H, const double *m, int64_t n, int64_t k_turn,
+                          double *hc_down, double *hc_up)
+{
+    double d = crossing(H, m, 0, k_turn, 1);
+    double u = crossing(H, m, k_turn, n - 1, 0);
+    if (hc_down) *hc_down = d;
+    if (hc_up) *hc_up = u;
+    return 0.5 * (fabs(d) + fabs(u));
+}
+
+/* Loop area |closed integral of m dH| by the trapezoid rule over consecutive samples. */
+double orc_loop_area(const double *H, const double *m, int64_t n)
+{
+    double s = 0.0;
+    for (int64_t k = 0; k + 1 < n; ++k) s += 0.5 * (m[k] + m[k + 1]) * (H[k + 1] - H[k]);
+    return fabs(s);
+}
+
+/* Mean loop, coercive field and area with delete-one jackknife standard errors over the
+ * realisations.  samples [n_real][n].  out: {Hc, Hc_se, area, area_se, Hc_down, Hc_up}.
+ * mean_out [n] (optional) receives the mean loop. */
+void orc_loop_stats(const double *H, const double *samples, int n_real, int64_t n, int64_t k_turn,
+                    double *out, double *mean_out)
+{
+    double *mean = (double *)calloc((size_t)n, sizeof(double));
+    double *loo = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int r = 0; r < n_real; ++r)
+        for (int64_t k = 0; k < n; ++k) mean[k] += samples[(int64_t)r * n + k];
+    for (int64_t k = 0; k < n; ++k) mean[k] /= (double)n_real;
+    double hd, hu;
+    double hc = orc_coercive_field(H, mean, n, k_turn, &hd, &hu);
+    double area = orc_loop_area(H, mean, n);
+    double hc_se = NAN, area_se = NAN;
+    if (n_real > 1) {
+        double *jh = (double *)malloc(sizeof(double) * (size_t)n_real);
+        double *ja = (double *)malloc(sizeof(double) * (size_t)n_real);
+        double mh = 0.0, ma = 0.0;
+        for (int r = 0; r < n_real; ++r) {
+            for (int64_t k = 0; k < n; ++k)
+                loo[k] = (mean[k] * n_real - samples[(int64_t)r * n + k]) / (double)(n_real - 1);
+            jh[r] = orc_coercive_field(H, loo, n, k_turn, NULL, NULL);
+            ja[r] = orc_loop_area(H, loo, n);
+            mh += jh[r];
+            ma += ja[r];
+        }
+        mh /= n_real;
+        ma /= n_real;
+        double vh = 0.0, va = 0.0;
+        for (int r = 0; r < n_real; ++r) {
+            vh += (jh[r] - mh) * (jh[r] - mh);
+            va += (ja[r] - ma) * (ja[r] - ma);
+        }
+        hc_se = sqrt((double)(n_real - 1) / n_real * vh);
+        area_se = sqrt((double)(n_real - 1) / n_real * va);
+        free(jh);
+        free(ja);
+    }
+    out[0] = hc;
+    out[1] = hc_se;
+    out[2] = area;
+    out[3] = area_se;
+    out[4] = hd;
+    out[5] = hu;
+    if (mean_out) memcpy(mean_out, mean, sizeof(double) * (size_t)n);
+    free(mean);
+    free(loo);
+}
+
+/* Specific loss power (W/g) from a loop area S in Oe: f mu0 (1000/4 pi) Ms S / rho, with rho in
+ * g/cm^3 (energy per cycle per volume times frequency, divided by the density). */
+double orc_specific_loss_power(double f_hz, double Ms, double S_Oe, double rho_g_cm3)
+{
+    double w_per_m3 = f_hz * ORC_MU0 * ORC_OE_TO_AM * Ms * S_Oe;
+    return w_per_m3 / (rho_g_cm3 * 1.0e6);
+}
