@@ -1,0 +1,366 @@
+"""Benchmark of the stochastic-LLG hysteresis-loop path on GB300.
+
+Workload (a step): the full-resolution magnetite rod at b = 1 (8x24x56 = 10752 cells of
+a0 = 0.839 nm), 256 noise realisations, T = 310 K, alpha = 0.1, dt = 2 fs, field swept
++-1500 Oe at 100 Oe/ns; one step advances all 256 rods by one sample interval (5000 Heun steps,
+1 Oe of sweep) in one persistent launch of the resident engine and writes one M(H) sample per rod.
+Inputs are synthetic (the rods start saturated along +z; the noise is Philox-generated).
+
+Reported: cell-steps/s (value), loops/s, the plain one-launch-per-half-step engine on the same
+workload, the small-rod (b = 4, 4 realisations) resident/plain ratio, an end-to-end figure through
+the C ABI with host buffers, the roofline of the resident kernel, and the FP64 oracle timed on the
+host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sLLG cell-steps/s and loops/s on 1 GB300 (batched vs plain); adjoint grads/s"
+UNIT = "cell-steps/s"
+WORKLOAD = "rod_b1_256real"
+L2_BYTES = 129 * 1024 * 1024
+SM_COUNT_NOMINAL = 152
+ALU_LANES_PER_SM = 128
+MAX_SM_MHZ = 2070.0
+# Algorithmic 32-bit lane operations of one cell-step (FMA-fused count of the method's
+# arithmetic: Philox4x32-10 98, uniforms 12, Box-Muller 20, two effective fields 40, two torques
+# 30, predictor with renormalisation and accumulator 12, corrector with renormalisation 9).
+ALU_OPS_PER_CELL_STEP = 221
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_grid(pkg, cfg, engine):
+    from workloads import MAGNETITE as M
+    g = pkg.Grid(*cfg["dims"], a0=M["a0"], b=cfg["b"])
+    g.set_material(A0=M["A0"], Ms=M["Ms"], K0=M["K0"], alpha=M["alpha"], T=M["T"])
+    g.set_scaling(mode=cfg["mode"], Tc=M["Tc"])
+    g.set_sweep(H_start=cfg["H_start"], H_turn=cfg["H_turn"], rate=cfg["rate"], dt=cfg["dt"],
+                sample_dH=cfg["sample_dH"])
+    g.set_engine(engine)
+    return g
+
+
+def timed_steps(torch, fn, K, W, flush):
+    """W warm-up calls, then K calls each bracketed by CUDA events on the current stream, with an
+    L2 flush (a write larger than L2) between calls outside the timed window."""
+    st = torch.cuda.current_stream()
+    for _ in range(W):
+        fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(K):
+        flush.add_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    torch.cuda.synchronize()
+    return times
+
+
+def cpu_oracle_rate(cfg, budget_s=12.0):
+    """The FP64 oracle on the host cores on a bounded sample of the workload: rods of the same
+    size, a short window of Heun steps.  Returns (cell-steps/s, threads, description)."""
+    from oracle import oracle as O
+    from workloads import MAGNETITE as M
+    O.build()
+    threads = os.cpu_count() or 1
+    p = O.material_problem(*cfg["dims"], a0=M["a0"], b=cfg["b"], A0=M["A0"], K0=M["K0"],
+                           Ms=M["Ms"], alpha=M["alpha"], T=M["T"], dt=cfg["dt"], mode=cfg["mode"],
+                           Tc=M["Tc"], H_start_Oe=cfg["H_start"], H_turn_Oe=cfg["H_turn"],
+                           rate_Oe_per_ns=cfg["rate"])
+    n_real = threads
+    # calibrate on a short run, then size the measured run to the budget
+    m = O.uniform_state(n_real, p.ncells)
+    t0 = time.perf_counter()
+    O.run(p, m, seed=cfg["seed"], n_steps=20, threads=threads)
+    per_step = (time.perf_counter() - t0) / 20
+    steps = max(20, int(budget_s / max(per_step, 1e-9)))
+    m = O.uniform_state(n_real, p.ncells)
+    t0 = time.perf_counter()
+    O.run(p, m, seed=cfg["seed"], n_steps=steps, threads=threads)
+    el = time.perf_counter() - t0
+    rate = n_real * p.ncells * steps / el
+    return rate, threads, (f"{n_real} b={cfg['b']} rods ({p.ncells} cells) x {steps} Heun steps "
+                           f"from +z, FP64, {el:.1f} s")
+
+
+# ------------------------------------------------------------------------------------------------
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle (the only other implementation of the method here)
+    timed on the host cores, per step a bounded sample of the same workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from workloads import CONFIGS
+    cfg = CONFIGS[WORKLOAD]
+    per_step_budget = max(2.0, min(20.0, 100.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(cfg, budget_s=per_step_budget / 4)
+    rates = []
+    desc = ""
+    threads = os.cpu_count() or 1
+    for _ in range(args.steps):
+        r, threads, desc = cpu_oracle_rate(cfg, budget_s=per_step_budget)
+        rates.append(r)
+    value = statistics.mean(rates)
+    ncell = math.prod(cfg["dims"])
+    steps_per_sample = round(cfg["sample_dH"] / (cfg["rate"] * 1e9 * cfg["dt"]))
+    step_cells = cfg["n_real"] * ncell * steps_per_sample
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_cells / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "rods": cfg["n_real"],
+                                        "cells_per_rod": ncell, "heun_steps_per_step": steps_per_sample,
+                                        "l2": "not applicable (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_1912_00310_gb300 as pkg
+    from workloads import CONFIGS
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    cfg = CONFIGS[WORKLOAD]
+    n_real = cfg["n_real"]
+    ncell = math.prod(cfg["dims"])
+    g = make_grid(pkg, cfg, pkg.ENGINE_RESIDENT)
+    S_per_step = g.sample_every  # Heun steps per bench step (one sample)
+    # each rank simulates its own 256 realisations (keys offset by rank): weak scaling
+    g.reset(seed=cfg["seed"], n_real=n_real, real_offset=rank * n_real)
+    samples = torch.zeros((n_real, g.n_samples), device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, device="cuda")
+
+    def step():
+        g.advance(S_per_step, samples)
+
+    clocks = Clocks(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times = timed_steps(torch, step, args.steps, args.warmup, flush)
+    clk = clocks.stop()
+    g.sync(600)
+    local_total = sum(times)
+    if world > 1:
+        t = torch.tensor([local_total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+        torch.distributed.barrier()
+    else:
+        total = local_total
+    cells_per_step = n_real * ncell * S_per_step
+    value = cells_per_step * args.steps * world / total
+    steps_per_loop = g.steps_per_loop
+    loops_per_s = value / (ncell * steps_per_loop)
+    launch_s = local_total / args.steps  # one persistent launch per step
+    achieved = ALU_OPS_PER_CELL_STEP * cells_per_step / launch_s
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm_count * ALU_LANES_PER_SM * MAX_SM_MHZ * 1e6
+
+    extra = {}
+    if not args.quick:
+        extra = side_measurements(args, torch, pkg, cfg, g, samples, S_per_step, flush)
+        local_rate = cells_per_step * args.steps / local_total
+        extra["plain_same_workload"]["resident_over_plain"] = (
+            local_rate / extra["plain_same_workload"]["value"])
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            r, threads, desc = cpu_oracle_rate(cfg)
+            cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rods_per_gpu": n_real, "cells_per_rod": ncell,
+                       "heun_steps_per_step": S_per_step, "engine": "resident (plane-pipelined)",
+                       "parallelism": f"replicas x{world} (independent realisations)",
+                       "l2": "flushed between steps (write of 2x L2)"},
+            "loops_per_s": loops_per_s,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
+                         "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "rod_pipelined_kernel",
+                         "ops_per_cell_step": ALU_OPS_PER_CELL_STEP,
+                         "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x {MAX_SM_MHZ:.0f} MHz"},
+            "clocks": clk,
+            "gpu_launches": args.steps,
+            "cpu_baseline": cpu,
+        }
+        line.update(extra)
+        print(json.dumps(line))
+    g.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def side_measurements(args, torch, pkg, cfg, g, samples, S_per_step, flush):
+    """End-to-end through the C ABI with host buffers, the plain engine on the same workload, and
+    the small-rod resident/plain ratio."""
+    import numpy as np
+    out = {}
+    n_real = cfg["n_real"]
+    ncell = math.prod(cfg["dims"])
+    # e2e: per step, the state goes host -> device, one sample interval runs, and the state and
+    # the new sample come back to the host (pinned buffers)
+    m_host = torch.empty((n_real, ncell, 3), dtype=torch.float32).pin_memory()
+    s_host = torch.empty((n_real,), dtype=torch.float32).pin_memory()
+    g.get_state(m_host)
+    step_idx = [g.step]
+
+    def e2e_step():
+        g.set_state(m_host, step_idx[0])
+        g.advance(S_per_step, samples)
+        k = (step_idx[0] + S_per_step) // S_per_step
+        s_host.copy_(samples[:, min(k, g.n_samples - 1)], non_blocking=True)
+        g.get_state(m_host)  # synchronises
+        step_idx[0] += S_per_step
+
+    for _ in range(2):
+        e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    el = time.perf_counter() - t0
+    out["e2e"] = {"value": n_real * ncell * S_per_step * args.steps / el, "unit": UNIT,
+                  "h2d_bytes_per_step": m_host.numel() * 4,
+                  "d2h_bytes_per_step": m_host.numel() * 4 + s_host.numel() * 4}
+    # plain engine on the same b = 1 workload, bounded window
+    gp = make_grid(pkg, cfg, pkg.ENGINE_PLAIN)
+    gp.reset(seed=cfg["seed"], n_real=n_real)
+    win = 100
+    ts = timed_steps(torch, lambda: gp.advance(win, samples), 3, 1, flush)
+    plain_rate = n_real * ncell * win * 3 / sum(ts)
+    gp.close()
+    # small rods (b = 4, 4 realisations, config of the plain-Heun workload)
+    from workloads import CONFIGS
+    c1 = CONFIGS["rod_b4_4real"]
+    ncell1 = math.prod(c1["dims"])
+    res = {}
+    for name, eng, win1 in (("resident", pkg.ENGINE_RESIDENT, 20000), ("plain", pkg.ENGINE_PLAIN, 2000)):
+        g1 = make_grid(pkg, c1, eng)
+        g1.reset(seed=c1["seed"], n_real=c1["n_real"])
+        s1 = torch.zeros((c1["n_real"], g1.n_samples), device="cuda")
+        t1 = timed_steps(torch, lambda: g1.advance(win1, s1), 3, 1, flush)
+        res[name] = c1["n_real"] * ncell1 * win1 * 3 / sum(t1)
+        spl = g1.steps_per_loop
+        g1.close()
+    out["plain_same_workload"] = {"value": plain_rate, "unit": UNIT,
+                                  "resident_over_plain": None}
+    out["small_rod_b4_4real"] = {
+        "resident_cell_steps_per_s": res["resident"], "plain_cell_steps_per_s": res["plain"],
+        "resident_over_plain": res["resident"] / res["plain"],
+        "resident_loops_per_s": res["resident"] / (ncell1 * spl),
+        "plain_loops_per_s": res["plain"] / (ncell1 * spl)}
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * llg.h -- C ABI of the GB300 stochastic-LLG hysteresis-loop library.
+ *
+ * The library time-steps the stochastic Landau-Lifshitz-Gilbert equation (Eq. 1 of Behbahani,
+ * Plumer & Saika-Voivod, "Coarse-graining in micromagnetic simulations of dynamic hysteresis
+ * loops", arXiv:1912.00310) on cubic grids of macrospin cells and builds averaged M(H) loops over
+ * many independent noise realisations (the realisation count paragraph after the field-sweep
+ * definition), at any coarse-graining level b with the parameter map of Eqs. 8-13.
+ *
+ * Conventions
+ *   - SI units, except fields, which are in Oe at the API (as in the paper; 1 Oe = 1000/4pi A/m).
+ *   - A cell index is  x + nx * (y + ny * z).  A state is float m[n_real][ncells][3] of unit
+ *     vectors (AoS).  A sample array is float m_samples[n_real][n_samples].
+ *   - Every call that enqueues GPU work does so on the context's CUDA stream (set at creation
+ *     or with llg_set_stream; NULL means the legacy default stream) and returns without waiting,
+ *     unless it says otherwise.  Pointers documented as "device" must be device memory of the
+ *     context's device; pointers documented as "host or device" are classified with
+ *     cudaPointerGetAttributes and copied through library-owned device buffers when on the host
+ *     (such calls synchronise the stream).
+ *   - No call throws.  Each returns an llg_status; on failure llg_last_error() holds a message
+ *     (thread-local, valid until the next failing call on the same thread).
+ *   - The library allocates device memory for the ensemble state and its own scratch with
+ *     cudaMalloc; the context owns it and llg_destroy frees it.  Output buffers are owned by the
+ *     caller.
+ *   - Thread safety: a context must not be used from two threads at once.  Distinct contexts
+ *     are independent.
+ */
+#ifndef LLG_H
+#define LLG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct llg_ctx llg_ctx;
+
+typedef enum llg_status {
+    LLG_OK = 0,
+    LLG_EINVAL = 1,        /* bad argument or call order                                    */
+    LLG_ENOMEM = 2,        /* device or host allocation failed                              */
+    LLG_ECUDA = 3,         /* a CUDA runtime call failed (message carries cudaGetErrorString) */
+    LLG_ENONFINITE = 4,    /* a non-finite magnetisation was found                          */
+    LLG_ETIMEOUT = 5,      /* llg_sync gave up waiting                                      */
+    LLG_EUNSUPPORTED = 6   /* valid request that no engine of this build handles            */
+} llg_status;
+
+/* Integration engines (all compute the same Heun step; they differ only in where the state
+ * lives between steps). */
+typedef enum llg_engine {
+    LLG_ENGINE_AUTO = 0,      /* resident when the grid fits on chip, else streaming          */
+    LLG_ENGINE_RESIDENT = 1,  /* persistent kernel, whole rods in shared memory, one launch  */
+    LLG_ENGINE_PLAIN = 2,     /* global-memory state, a predictor and a corrector launch per step */
+    LLG_ENGINE_STREAM = 3     /* HBM stencil for grids larger than shared memory             */
+} llg_engine;
+
+/* Loop observables of one ensemble (raw = at level b; "0" = mapped back to the unscaled system
+ * with H0 = H / zeta (Eq. 10) and m0 = rescale * m (Eq. 11 or Eq. 13)). */
+typedef struct llg_loop_stats {
+    double Hc_Oe, Hc_se_Oe;        /* coercive field (|Hc_down| + |Hc_up|) / 2, jackknife SE */
+    double area_Oe, area_se_Oe;    /* |closed integral of m dH| (trapezoid), jackknife SE     */
+    double Hc_down_Oe, Hc_up_Oe;   /* zero crossings of the mean loop on each branch         */
+    double zeta, m_rescale;        /* factors of the selected scaling mode                   */
+    double Hc0_Oe, area0_Oe;       /* rescaled coercive field and area                       */
+} llg_loop_stats;
+
+/* Number of doubles written by llg_get_coefficients. */
+#define LLG_NCOEFF 16
+
+/* ---------------------------------------------------------------------------------------- */
+/* Context                                                                                   */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Create a grid of nx * ny * nz cubic cells of edge b * a0_m (the rod of the simulation-cell
+ * paragraph is 8x24x56 cells of a0 = 0.839 nm at b = 1 and (8/b)x(24/b)x(56/b) at level b).
+ * periodic_mask: bit 0 x, bit 1 y, bit 2 z; free faces otherwise.  device: CUDA ordinal.
+ * cuda_stream: a cudaStream_t (may be NULL).  *out receives the context.
+ * Errors: EINVAL (non-positive sizes, b < 1, a0 <= 0, more than 2^31 cells), ECUDA. */
+llg_status llg_create_grid(llg_ctx **out, int nx, int ny, int nz, double a0_m, int b,
+                           unsigned periodic_mask, int device, void *cuda_stream);
+
+/* Free all device memory of the context (waits for its stream).  NULL is ignored. */
+void llg_destroy(llg_ctx *ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *llg_last_error(void);
+
+/* Replace the stream on which the context enqueues work. */
+llg_status llg_set_stream(llg_ctx *ctx, void *cuda_stream);
+
+/* Material parameters of the unscaled (b = 1) system, material paragraph and Eq. 1:
+ * A0 exchange stiffness (J/m), Ms saturation magnetisation (A/m), K0 uniaxial anisotropy
+ * (J/m^3) along the unit vector u, alpha Gilbert damping, T temperature (K).  The engines of this
+ * build support u = +z or -z only (EUNSUPPORTED otherwise); the paper's 5-degree axis
+ * dispersion is not modelled.  Errors: EINVAL (Ms <= 0, alpha < 0, T < 0, A0 < 0, |u| = 0). */
+llg_status llg_set_material(llg_ctx *ctx, double A0, double Ms, double K0, const double u[3],
+                            double alpha, double T_kelvin);
+
+/* Coarse-graining map, Eqs. 8-13.  mode 0: A and K unchanged (Fig. 2a); mode 1: A(b) = zeta A0,
+ * K(b) = zeta^3 K0 and m0 = zeta m (Eqs. 8-11); mode 2: as mode 1 with m0 = (delta zeta + 1 -
+ * delta) m (Eq. 13).  zeta(b) = t/b + 1 - t, t = T / Tc.  scale = {s_K, s_alpha, s_Ms} multiplies
+ * K(b), alpha and Ms (NULL means {1, 1, 1}).  Default: mode 1, Tc = 858 K, delta = 0.511.
+ * Errors: EINVAL (mode outside 0..2, Tc <= 0, a scale factor <= 0). */
+llg_status llg_set_scaling(llg_ctx *ctx, int mode, double Tc_kelvin, double delta,
+                           const double scale[3]);
+
+/* Zeeman field along z (the field-sweep paragraph): a triangle wave H_start -> H_turn -> H_start
+ * at |dH/dt| = rate (Oe/ns), time step dt_s (s), one M(H) sample every sample_dH_Oe of sweep.
+ * A full loop is 2 |H_start - H_turn| / (rate dt) steps and 2 |H_start - H_turn| / sample_dH + 1
+ * samples, sample k taken after step k * sample_every (sample 0 is the initial state).
+ * rate = 0 (or H_start = H_turn) holds the field at H_start; sample_dH then counts steps.
+ * shape: 0 = triangle (1 = the paper's sinusoid is not built: EUNSUPPORTED).
+ * Errors: EINVAL (dt <= 0, rate < 0, the span or the sample spacing not a whole number of steps
+ * to 1e-6 relative). */
+llg_status llg_set_sweep(llg_ctx *ctx, double H_start_Oe, double H_turn_Oe, double rate_Oe_per_ns,
+                         double dt_s, double sample_dH_Oe, int shape);
+
+/* Select the integration engine (llg_engine).  Errors: EINVAL, EUNSUPPORTED (the engine cannot
+ * hold this grid: checked at the next reset/advance). */
+llg_status llg_set_engine(llg_ctx *ctx, int engine);
+
+/* Launch-shape overrides of the resident engine (0 = automatic, the default):
+ *   LLG_TUNE_ROD_KIND      1 two-phase kernel, 2 plane-pipelined kernel
+ *   LLG_TUNE_RODS_PER_CTA  rods per CTA of the two-phase kernel
+ *   LLG_TUNE_CHUNK_STEPS   Heun steps per launch (default 2^20)
+ * The arithmetic, and so the trajectory, does not depend on these.  Errors: EINVAL (unknown
+ * key, negative value); EUNSUPPORTED at the next advance if the shape cannot hold the grid. */
+#define LLG_TUNE_ROD_KIND 1
+#define LLG_TUNE_RODS_PER_CTA 2
+#define LLG_TUNE_CHUNK_STEPS 3
+llg_status llg_set_tuning(llg_ctx *ctx, int key, int64_t value);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Ensemble runs                                                                             */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Start an ensemble of n_real realisations r = 0..n_real-1 with noise keys
+ * (seed, real_offset + r): every cell m = +z (saturated along the initial field), step 0.
+ * Allocates the state (n_real * ncells * 12 bytes).  Errors: EINVAL (n_real < 1, material or
+ * sweep not set), ENOMEM, ECUDA. */
+llg_status llg_reset(llg_ctx *ctx, uint32_t seed, int n_real, uint32_t real_offset);
+
+/* Advance the ensemble by n_steps Heun steps of Eq. 1 with the Brown thermal field: per step n
+ * and cell i, three standard normals from Philox4x32-10 (key = (seed, realisation), counter =
+ * (i, n mod 2^32, n >> 32, 0)) and Box-Muller on 24-bit uniforms, times
+ * sigma = sqrt(2 alpha kB T / (gamma0 mu0 Ms V dt)); predictor m~ = |m + dt f(m, t_n)|^-1 (...),
+ * corrector m <- normalise(m + dt/2 (f(m, t_n) + f(m~, t_n+1))) with the same thermal field.
+ * m_samples: device [n_real][n_samples] (llg_num_samples) or NULL; the cell-averaged m_z after
+ * every step index that is a multiple of sample_every and below n_samples * sample_every is
+ * written at its sample column; other columns are left untouched.  Asynchronous.
+ * Errors: EINVAL (no ensemble, n_steps < 0), EUNSUPPORTED, ECUDA. */
+llg_status llg_advance(llg_ctx *ctx, int64_t n_steps, float *m_samples);
+
+/* One full loop per realisation: llg_reset(seed, n_real, real_offset), sample 0 = 1 (the +z
+ * start), then llg_advance(llg_steps_per_loop).  m_samples: host or device
+ * [n_real][n_samples] (caller-owned, required).  stats (host, optional): when given, the call
+ * synchronises and fills the loop observables of the mean loop.  Errors: as llg_reset and
+ * llg_advance. */
+llg_status llg_run_loops(llg_ctx *ctx, uint32_t seed, int n_real, uint32_t real_offset,
+                         float *m_samples, llg_loop_stats *stats);
+
+/* Copy the ensemble state out to m (host or device [n_real][ncells][3]) and its step index
+ * (optional).  Synchronises when m is host memory. */
+llg_status llg_get_state(llg_ctx *ctx, float *m, int64_t *step);
+
+/* Replace the ensemble state from m (host or device [n_real][ncells][3], unit vectors) at step
+ * index `step`.  Resuming at step n with the same keys reproduces the uninterrupted run
+ * bitwise (the noise is a function of (seed, realisation, cell, step) only). */
+llg_status llg_set_state(llg_ctx *ctx, const float *m, int64_t step);
+
+/* Wait for the context's stream, giving up after timeout_s seconds (<= 0: wait forever) with
+ * LLG_ETIMEOUT.  Errors from earlier asynchronous work surface here as ECUDA. */
+llg_status llg_sync(llg_ctx *ctx, double timeout_s);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Queries and host-side loop analysis                                                       */
+/* ---------------------------------------------------------------------------------------- */
+
+int64_t llg_num_cells(const llg_ctx *ctx);
+int64_t llg_num_samples(const llg_ctx *ctx);      /* samples of one full loop             */
+int64_t llg_steps_per_loop(const llg_ctx *ctx);   /* 2 * steps from H_start to H_turn     */
+int64_t llg_sample_every(const llg_ctx *ctx);     /* steps between samples                */
+int64_t llg_current_step(const llg_ctx *ctx);
+int llg_active_engine(const llg_ctx *ctx);        /* engine the next advance will use     */
+
+/* Simulation-level coefficients (FP64) in this order: zeta, A(b), K(b), Ms, alpha, a, V,
+ * gamma0 = mu0 ge, gamma1 = gamma0/(1+alpha^2), alpha*gamma1, c_ex = 2A/(mu0 Ms a^2),
+ * c_an = 2K/(mu0 Ms), sigma, H_start (A/m), dH per step (A/m), m_rescale. */
+llg_status llg_get_coefficients(const llg_ctx *ctx, double out[LLG_NCOEFF]);
+
+/* Field (Oe) of every sample of one full loop: H_Oe host [llg_num_samples]. */
+llg_status llg_sample_fields(const llg_ctx *ctx, double *H_Oe);
+
+/* Loop observables of host samples [n_real][n_samples] taken at fields H_Oe [n_samples], the
+ * descending branch ending at sample k_turn: mean loop, coercive field from the first zero
+ * crossing on each branch (linear interpolation), trapezoid area, delete-one jackknife standard
+ * errors (paragraph on the Fig. 2 loops: "one standard error"), and the rescaled values for
+ * scaling mode / zeta / delta (Eqs. 10, 11, 13).  mean_out (optional) host [n_samples].
+ * Errors: EINVAL. */
+llg_status llg_loop_stats_host(const float *m_samples, int n_real, int64_t n_samples,
+                               const double *H_Oe, int64_t k_turn, int mode, double zeta,
+                               double delta, llg_loop_stats *out, double *mean_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LLG_H */

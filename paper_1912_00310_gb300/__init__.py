@@ -1,0 +1,177 @@
+"""GB300-native stochastic-LLG hysteresis-loop library (arXiv:1912.00310, coarse-grained
+micromagnetic loops).  Python view of the C ABI in include/llg.h.
+
+PyTorch supplies device memory and streams; every step of the integration runs in libllg.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (COEFF_NAMES, ENGINE_AUTO, ENGINE_PLAIN, ENGINE_RESIDENT, ENGINE_STREAM,
+                   TUNE_CHUNK_STEPS, TUNE_ROD_KIND, TUNE_RODS_PER_CTA, LLGError, LoopStats)
+
+__all__ = ["Grid", "LLGError", "LoopStats", "loop_stats", "ENGINE_AUTO", "ENGINE_RESIDENT",
+           "ENGINE_PLAIN", "ENGINE_STREAM", "TUNE_ROD_KIND", "TUNE_RODS_PER_CTA", "TUNE_CHUNK_STEPS",
+           "library"]
+
+
+def library():
+    """The loaded libllg.so (raises ImportError if it has not been built)."""
+    return _lib.load()
+
+
+def _ptr(x) -> int:
+    """Address of a torch tensor (device or host) or a numpy array."""
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return x.ctypes.data
+    assert x.is_contiguous()
+    return x.data_ptr()
+
+
+def _current_stream(device: int):
+    import torch
+    if not torch.cuda.is_available():
+        return None
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Grid:
+    """One grid of nx*ny*nz cubic cells of edge b*a0 (context of the C ABI)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, *, a0: float, b: int = 1, periodic: int = 0,
+                 device: int = 0, stream=None):
+        L = _lib.load()
+        self._L = L
+        h = C.c_void_p()
+        st = stream if stream is not None else _current_stream(device)
+        _lib.check(L.llg_create_grid(C.byref(h), nx, ny, nz, a0, b, periodic, device, st))
+        self._h = h
+        self.dims = (nx, ny, nz)
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.llg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- setup -------------------------------------------------------------------------
+    def set_stream(self, stream):
+        _lib.check(self._L.llg_set_stream(self._h, stream))
+
+    def set_material(self, *, A0, Ms, K0, alpha, T, u=(0.0, 0.0, 1.0)):
+        uu = (C.c_double * 3)(*u)
+        _lib.check(self._L.llg_set_material(self._h, A0, Ms, K0, uu, alpha, T))
+        return self
+
+    def set_scaling(self, mode=1, Tc=858.0, delta=0.511, scale=(1.0, 1.0, 1.0)):
+        s = (C.c_double * 3)(*scale)
+        _lib.check(self._L.llg_set_scaling(self._h, mode, Tc, delta, s))
+        return self
+
+    def set_sweep(self, *, H_start, H_turn, rate, dt, sample_dH=1.0, shape=0):
+        _lib.check(self._L.llg_set_sweep(self._h, H_start, H_turn, rate, dt, sample_dH, shape))
+        return self
+
+    def set_engine(self, engine: int):
+        _lib.check(self._L.llg_set_engine(self._h, engine))
+        return self
+
+    def set_tuning(self, key: int, value: int):
+        _lib.check(self._L.llg_set_tuning(self._h, key, int(value)))
+        return self
+
+    # ---- queries -----------------------------------------------------------------------
+    @property
+    def ncells(self) -> int:
+        return self._L.llg_num_cells(self._h)
+
+    @property
+    def n_samples(self) -> int:
+        return self._L.llg_num_samples(self._h)
+
+    @property
+    def steps_per_loop(self) -> int:
+        return self._L.llg_steps_per_loop(self._h)
+
+    @property
+    def sample_every(self) -> int:
+        return self._L.llg_sample_every(self._h)
+
+    @property
+    def step(self) -> int:
+        return self._L.llg_current_step(self._h)
+
+    @property
+    def engine(self) -> int:
+        return self._L.llg_active_engine(self._h)
+
+    def coefficients(self) -> dict:
+        out = (C.c_double * len(COEFF_NAMES))()
+        _lib.check(self._L.llg_get_coefficients(self._h, out))
+        return dict(zip(COEFF_NAMES, list(out)))
+
+    def sample_fields(self) -> np.ndarray:
+        H = np.zeros(self.n_samples)
+        _lib.check(self._L.llg_sample_fields(self._h, H.ctypes.data_as(C.POINTER(C.c_double))))
+        return H
+
+    # ---- ensemble ----------------------------------------------------------------------
+    def reset(self, seed: int, n_real: int, real_offset: int = 0):
+        _lib.check(self._L.llg_reset(self._h, seed, n_real, real_offset))
+
+    def advance(self, n_steps: int, samples=None):
+        """samples: device tensor float32 [n_real][n_samples] or None."""
+        _lib.check(self._L.llg_advance(self._h, int(n_steps),
+                                       C.c_void_p(_ptr(samples)) if samples is not None else None))
+
+    def run_loops(self, seed: int, n_real: int, samples, real_offset: int = 0, stats=True):
+        """One full loop per realisation into samples (device tensor or host array, float32
+        [n_real][n_samples]); returns the loop observables when stats is true."""
+        st = LoopStats()
+        _lib.check(self._L.llg_run_loops(self._h, seed, n_real, real_offset,
+                                         C.c_void_p(_ptr(samples)),
+                                         C.byref(st) if stats else None))
+        return st.as_dict() if stats else None
+
+    def get_state(self, out):
+        step = C.c_int64()
+        _lib.check(self._L.llg_get_state(self._h, C.c_void_p(_ptr(out)), C.byref(step)))
+        return step.value
+
+    def set_state(self, m, step: int):
+        _lib.check(self._L.llg_set_state(self._h, C.c_void_p(_ptr(m)), int(step)))
+
+    def sync(self, timeout_s: float = 0.0):
+        _lib.check(self._L.llg_sync(self._h, timeout_s))
+
+
+def loop_stats(samples: np.ndarray, H: np.ndarray, k_turn: int, mode=1, zeta=1.0, delta=0.511):
+    """Host loop observables of float32 samples [n_real][n_samples] (library implementation)."""
+    L = _lib.load()
+    s = np.ascontiguousarray(samples, dtype=np.float32)
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    out = LoopStats()
+    mean = np.zeros(s.shape[1])
+    _lib.check(L.llg_loop_stats_host(s.ctypes.data, s.shape[0], s.shape[1],
+                                     H.ctypes.data_as(C.POINTER(C.c_double)), int(k_turn), mode,
+                                     zeta, delta, C.byref(out),
+                                     mean.ctypes.data_as(C.POINTER(C.c_double))))
+    d = out.as_dict()
+    d["mean"] = mean
+    return d

@@ -1,0 +1,504 @@
+// api.cpp -- the C ABI (include/llg.h): contexts, parameter setup, ensemble state, engine
+// selection and host/device marshalling.  All arithmetic of a step runs in the CUDA engines.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/llg.h"
+#include "llg_internal.h"
+
+struct llg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int nx = 0, ny = 0, nz = 0, b = 1;
+    unsigned periodic = 0;
+    double a0 = 0.0;
+    bool has_material = false, has_sweep = false;
+    llg::MaterialIn mat{};
+    llg::ScalingIn sc{1, 858.0, 0.511, 1.0, 1.0, 1.0};
+    llg::SweepIn sw{};
+    int engine = LLG_ENGINE_AUTO;
+    int tune_kind = 0, tune_rods = 0;
+    long long chunk_steps = 1LL << 20;
+    // ensemble
+    int n_real = 0;
+    uint32_t seed = 0, real0 = 0;
+    long long step = 0;
+    float *d_m = nullptr;        // [n_real][ncells][3]
+    size_t m_cap = 0;            // floats
+    float *d_scratch = nullptr;  // plain engine: mt, acc, hth
+    size_t scratch_cap = 0;
+    float *d_samples = nullptr;  // staging for host sample buffers
+    size_t samples_cap = 0;
+    int *d_status = nullptr;
+    long long launches = 0;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+llg_status fail(llg_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+llg_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(LLG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LLG_CUDA(call, what)                        \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+long long ncells_of(const llg_ctx *c) { return (long long)c->nx * c->ny * c->nz; }
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+llg_status derived_of(const llg_ctx *c, llg::Derived *d)
+{
+    if (!c->has_material) return fail(LLG_EINVAL, "material not set (llg_set_material)");
+    if (!c->has_sweep) return fail(LLG_EINVAL, "sweep not set (llg_set_sweep)");
+    char err[256];
+    if (!llg::derive(c->b, c->a0, c->mat, c->sc, c->sw, d, err, sizeof err)) return fail(LLG_EINVAL, "%s", err);
+    return LLG_OK;
+}
+
+llg_status grow(float **buf, size_t *cap, size_t need_floats)
+{
+    if (*cap >= need_floats) return LLG_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(buf, need_floats * sizeof(float));
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        cudaGetLastError();
+        return fail(LLG_ENOMEM, "cudaMalloc of %zu bytes failed: %s", need_floats * sizeof(float),
+                    cudaGetErrorString(e));
+    }
+    *cap = need_floats;
+    return LLG_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int resolve_engine(const llg_ctx *c, const llg::KParams &kp, int n_real, llg::RodPlan *plan)
+{
+    const bool rod_ok = llg::rod_plan(kp, n_real, c->device, plan, c->tune_kind, c->tune_rods);
+    switch (c->engine) {
+        case LLG_ENGINE_RESIDENT:
+            return rod_ok ? LLG_ENGINE_RESIDENT : -1;
+        case LLG_ENGINE_PLAIN:
+            return LLG_ENGINE_PLAIN;
+        case LLG_ENGINE_STREAM:
+            return -1;
+        default:
+            return rod_ok ? LLG_ENGINE_RESIDENT : LLG_ENGINE_PLAIN;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *llg_last_error(void) { return g_err; }
+
+llg_status llg_create_grid(llg_ctx **out, int nx, int ny, int nz, double a0_m, int b,
+                           unsigned periodic_mask, int device, void *cuda_stream)
+{
+    if (!out) return fail(LLG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(LLG_EINVAL, "grid sizes must be positive");
+    if ((long long)nx * ny * nz > (1LL << 31)) return fail(LLG_EINVAL, "more than 2^31 cells");
+    if (!(a0_m > 0.0) || b < 1) return fail(LLG_EINVAL, "a0 must be > 0 and b >= 1");
+    if (periodic_mask > 7u) return fail(LLG_EINVAL, "periodic_mask uses bits 0-2 only");
+    // The device is only checked when a driver is present, so that parameter setup and the
+    // host-side queries also work on a machine without a GPU; the first call that needs the
+    // GPU (llg_reset) reports ECUDA there.
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) == cudaSuccess) {
+        if (device < 0 || device >= ndev)
+            return fail(LLG_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    } else {
+        cudaGetLastError();
+        if (device < 0) return fail(LLG_EINVAL, "device must be >= 0");
+    }
+    llg_ctx *c = new (std::nothrow) llg_ctx();
+    if (!c) return fail(LLG_ENOMEM, "context allocation failed");
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->a0 = a0_m;
+    c->b = b;
+    c->periodic = periodic_mask;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    *out = c;
+    return LLG_OK;
+}
+
+void llg_destroy(llg_ctx *c)
+{
+    if (!c) return;
+    if (!c->d_status && !c->d_m) {  // nothing was ever put on the device
+        delete c;
+        return;
+    }
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->d_m);
+    cudaFree(c->d_scratch);
+    cudaFree(c->d_samples);
+    cudaFree(c->d_status);
+    cudaGetLastError();
+    delete c;
+}
+
+llg_status llg_set_stream(llg_ctx *c, void *cuda_stream)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    c->stream = (cudaStream_t)cuda_stream;
+    return LLG_OK;
+}
+
+llg_status llg_set_material(llg_ctx *c, double A0, double Ms, double K0, const double u[3],
+                            double alpha, double T)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (!(Ms > 0.0) || !(alpha >= 0.0) || !(T >= 0.0) || !(A0 >= 0.0) || !std::isfinite(K0))
+        return fail(LLG_EINVAL, "need Ms > 0, alpha >= 0, T >= 0, A0 >= 0, finite K0");
+    if (u) {
+        const double n = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        if (!(n > 0.0)) return fail(LLG_EINVAL, "easy axis has zero length");
+        if (std::fabs(u[0]) > 1e-12 * n || std::fabs(u[1]) > 1e-12 * n)
+            return fail(LLG_EUNSUPPORTED, "only an easy axis along z is built (axis dispersion is not)");
+    }
+    c->mat = llg::MaterialIn{A0, Ms, K0, alpha, T};
+    c->has_material = true;
+    return LLG_OK;
+}
+
+llg_status llg_set_scaling(llg_ctx *c, int mode, double Tc, double delta, const double scale[3])
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (mode < 0 || mode > 2) return fail(LLG_EINVAL, "scaling mode must be 0, 1 or 2");
+    if (!(Tc > 0.0)) return fail(LLG_EINVAL, "Tc must be > 0");
+    double s[3] = {1.0, 1.0, 1.0};
+    if (scale)
+        for (int i = 0; i < 3; ++i) s[i] = scale[i];
+    for (double v : s)
+        if (!(v > 0.0) || !std::isfinite(v)) return fail(LLG_EINVAL, "scale factors must be > 0");
+    c->sc = llg::ScalingIn{mode, Tc, delta, s[0], s[1], s[2]};
+    return LLG_OK;
+}
+
+llg_status llg_set_sweep(llg_ctx *c, double H_start_Oe, double H_turn_Oe, double rate, double dt_s,
+                         double sample_dH_Oe, int shape)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (shape == 1) return fail(LLG_EUNSUPPORTED, "the sinusoidal sweep is not built");
+    if (shape != 0) return fail(LLG_EINVAL, "shape must be 0 (triangle)");
+    if (!(dt_s > 0.0) || !(rate >= 0.0) || !(sample_dH_Oe > 0.0) || !std::isfinite(H_start_Oe) ||
+        !std::isfinite(H_turn_Oe))
+        return fail(LLG_EINVAL, "need dt > 0, rate >= 0, sample spacing > 0");
+    llg::SweepIn sw{H_start_Oe, H_turn_Oe, rate, dt_s, sample_dH_Oe};
+    // validate now so that errors surface at the call that caused them
+    const llg::MaterialIn mat = c->has_material ? c->mat : llg::MaterialIn{1e-11, 1e5, 0.0, 0.1, 0.0};
+    llg::Derived d;
+    char err[256];
+    if (!llg::derive(c->b, c->a0, mat, c->sc, sw, &d, err, sizeof err)) return fail(LLG_EINVAL, "%s", err);
+    c->sw = sw;
+    c->has_sweep = true;
+    return LLG_OK;
+}
+
+llg_status llg_set_engine(llg_ctx *c, int engine)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (engine < LLG_ENGINE_AUTO || engine > LLG_ENGINE_STREAM) return fail(LLG_EINVAL, "unknown engine %d", engine);
+    c->engine = engine;
+    return LLG_OK;
+}
+
+llg_status llg_set_tuning(llg_ctx *c, int key, int64_t value)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (value < 0) return fail(LLG_EINVAL, "tuning values must be >= 0");
+    switch (key) {
+        case LLG_TUNE_ROD_KIND:
+            if (value > 2) return fail(LLG_EINVAL, "rod kernel kind must be 0, 1 or 2");
+            c->tune_kind = (int)value;
+            return LLG_OK;
+        case LLG_TUNE_RODS_PER_CTA:
+            if (value > 4096) return fail(LLG_EINVAL, "rods per CTA too large");
+            c->tune_rods = (int)value;
+            return LLG_OK;
+        case LLG_TUNE_CHUNK_STEPS:
+            c->chunk_steps = value > 0 ? value : (1LL << 20);
+            return LLG_OK;
+        default:
+            return fail(LLG_EINVAL, "unknown tuning key %d", key);
+    }
+}
+
+llg_status llg_reset(llg_ctx *c, uint32_t seed, int n_real, uint32_t real_offset)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (n_real < 1) return fail(LLG_EINVAL, "n_real must be >= 1");
+    llg::Derived d;
+    llg_status s = derived_of(c, &d);
+    if (s != LLG_OK) return s;
+    DeviceGuard g(c->device);
+    if (!c->d_status) LLG_CUDA(cudaMalloc(&c->d_status, sizeof(int)), "cudaMalloc(status)");
+    const size_t n = (size_t)n_real * (size_t)ncells_of(c) * 3;
+    s = grow(&c->d_m, &c->m_cap, n);
+    if (s != LLG_OK) return s;
+    // m = +z everywhere: fill the z components through the column helper (row stride 3)
+    LLG_CUDA(cudaMemsetAsync(c->d_m, 0, n * sizeof(float), c->stream), "cudaMemsetAsync(m)");
+    LLG_CUDA(llg::fill_column(c->d_m, (int)(n / 3), 3, 2, 1.0f, c->stream), "fill +z");
+    LLG_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "cudaMemsetAsync(status)");
+    c->n_real = n_real;
+    c->seed = seed;
+    c->real0 = real_offset;
+    c->step = 0;
+    return LLG_OK;
+}
+
+llg_status llg_advance(llg_ctx *c, int64_t n_steps, float *m_samples)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (c->n_real < 1 || !c->d_m) return fail(LLG_EINVAL, "no ensemble (llg_reset first)");
+    if (n_steps < 0) return fail(LLG_EINVAL, "n_steps must be >= 0");
+    if (m_samples && !is_device_ptr(m_samples)) return fail(LLG_EINVAL, "m_samples must be device memory");
+    llg::Derived d;
+    llg_status s = derived_of(c, &d);
+    if (s != LLG_OK) return s;
+    DeviceGuard g(c->device);
+    llg::KParams kp = llg::kparams_of(d, c->nx, c->ny, c->nz, c->periodic, c->sw.dt);
+    kp.seed = c->seed;
+    kp.real0 = c->real0;
+    llg::RodPlan plan{};
+    const int eng = resolve_engine(c, kp, c->n_real, &plan);
+    if (eng < 0) return fail(LLG_EUNSUPPORTED, "the selected engine cannot hold a %dx%dx%d grid", c->nx, c->ny, c->nz);
+    if (eng == LLG_ENGINE_RESIDENT) {
+        const long long chunk = c->chunk_steps;
+        for (long long done = 0; done < n_steps; done += chunk) {
+            const long long k = n_steps - done < chunk ? n_steps - done : chunk;
+            LLG_CUDA(llg::rod_advance(kp, plan, c->d_m, c->n_real, c->step + done, k, m_samples,
+                                      c->d_status, c->stream),
+                     "resident engine launch");
+            ++c->launches;
+        }
+    } else {
+        const size_t per = (size_t)c->n_real * (size_t)ncells_of(c) * 3;
+        s = grow(&c->d_scratch, &c->scratch_cap, 3 * per);
+        if (s != LLG_OK) return s;
+        LLG_CUDA(llg::plain_advance(kp, c->d_m, c->d_scratch, c->d_scratch + per, c->d_scratch + 2 * per,
+                                    c->n_real, c->step, n_steps, m_samples, c->d_status, c->stream,
+                                    &c->launches),
+                 "plain engine launch");
+    }
+    c->step += n_steps;
+    return LLG_OK;
+}
+
+llg_status llg_sync(llg_ctx *c, double timeout_s)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    DeviceGuard g(c->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(c->stream);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "stream");
+        if (timeout_s > 0.0) {
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > timeout_s) return fail(LLG_ETIMEOUT, "stream still busy after %.3f s", el);
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    int st = 0;
+    if (!c->d_status) return LLG_OK;
+    LLG_CUDA(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+    if (st) return fail(LLG_ENONFINITE, "a non-finite magnetisation was sampled");
+    return LLG_OK;
+}
+
+llg_status llg_run_loops(llg_ctx *c, uint32_t seed, int n_real, uint32_t real_offset, float *m_samples,
+                         llg_loop_stats *stats)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (!m_samples) return fail(LLG_EINVAL, "m_samples is required");
+    llg::Derived d;
+    llg_status s = derived_of(c, &d);
+    if (s != LLG_OK) return s;
+    if (d.steps_per_loop <= 0) return fail(LLG_EINVAL, "a loop needs a swept field (rate > 0)");
+    s = llg_reset(c, seed, n_real, real_offset);
+    if (s != LLG_OK) return s;
+    DeviceGuard g(c->device);
+    const bool dev = is_device_ptr(m_samples);
+    float *dst = m_samples;
+    const size_t ns = (size_t)n_real * (size_t)d.n_samples;
+    if (!dev) {
+        s = grow(&c->d_samples, &c->samples_cap, ns);
+        if (s != LLG_OK) return s;
+        dst = c->d_samples;
+    }
+    LLG_CUDA(llg::fill_column(dst, n_real, d.n_samples, 0, 1.0f, c->stream), "sample 0");
+    s = llg_advance(c, d.steps_per_loop, dst);
+    if (s != LLG_OK) return s;
+    if (!dev) {
+        LLG_CUDA(cudaMemcpyAsync(m_samples, dst, ns * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
+                 "samples to host");
+    }
+    if (stats || !dev) {
+        s = llg_sync(c, 0.0);
+        if (s != LLG_OK) return s;
+    }
+    if (stats) {
+        std::vector<float> host;
+        const float *hs = m_samples;
+        if (dev) {
+            host.resize(ns);
+            LLG_CUDA(cudaMemcpy(host.data(), m_samples, ns * sizeof(float), cudaMemcpyDeviceToHost), "samples");
+            hs = host.data();
+        }
+        std::vector<double> H((size_t)d.n_samples);
+        s = llg_sample_fields(c, H.data());
+        if (s != LLG_OK) return s;
+        s = llg_loop_stats_host(hs, n_real, d.n_samples, H.data(), d.n_half / d.sample_every, c->sc.mode,
+                                d.zeta, c->sc.delta, stats, nullptr);
+        if (s != LLG_OK) return fail(s, "loop statistics failed");
+    }
+    return LLG_OK;
+}
+
+llg_status llg_get_state(llg_ctx *c, float *m, int64_t *step)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (c->n_real < 1) return fail(LLG_EINVAL, "no ensemble");
+    if (step) *step = c->step;
+    if (!m) return LLG_OK;
+    DeviceGuard g(c->device);
+    const size_t bytes = (size_t)c->n_real * (size_t)ncells_of(c) * 3 * sizeof(float);
+    const bool dev = is_device_ptr(m);
+    LLG_CUDA(cudaMemcpyAsync(m, c->d_m, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+             "state copy out");
+    if (!dev) LLG_CUDA(cudaStreamSynchronize(c->stream), "state copy out");
+    return LLG_OK;
+}
+
+llg_status llg_set_state(llg_ctx *c, const float *m, int64_t step)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (c->n_real < 1) return fail(LLG_EINVAL, "no ensemble (llg_reset first)");
+    if (!m || step < 0) return fail(LLG_EINVAL, "need a state and step >= 0");
+    DeviceGuard g(c->device);
+    const size_t bytes = (size_t)c->n_real * (size_t)ncells_of(c) * 3 * sizeof(float);
+    const bool dev = is_device_ptr(m);
+    LLG_CUDA(cudaMemcpyAsync(c->d_m, m, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+             "state copy in");
+    if (!dev) LLG_CUDA(cudaStreamSynchronize(c->stream), "state copy in");
+    c->step = step;
+    return LLG_OK;
+}
+
+int64_t llg_num_cells(const llg_ctx *c) { return c ? ncells_of(c) : -1; }
+
+int64_t llg_num_samples(const llg_ctx *c)
+{
+    llg::Derived d;
+    if (!c || derived_of(c, &d) != LLG_OK) return -1;
+    return d.n_samples;
+}
+
+int64_t llg_steps_per_loop(const llg_ctx *c)
+{
+    llg::Derived d;
+    if (!c || derived_of(c, &d) != LLG_OK) return -1;
+    return d.steps_per_loop;
+}
+
+int64_t llg_sample_every(const llg_ctx *c)
+{
+    llg::Derived d;
+    if (!c || derived_of(c, &d) != LLG_OK) return -1;
+    return d.sample_every;
+}
+
+int64_t llg_current_step(const llg_ctx *c) { return c ? c->step : -1; }
+
+int llg_active_engine(const llg_ctx *c)
+{
+    llg::Derived d;
+    if (!c || derived_of(c, &d) != LLG_OK) return -1;
+    llg::KParams kp = llg::kparams_of(d, c->nx, c->ny, c->nz, c->periodic, c->sw.dt);
+    llg::RodPlan plan{};
+    return resolve_engine(c, kp, c->n_real > 0 ? c->n_real : 1, &plan);
+}
+
+llg_status llg_get_coefficients(const llg_ctx *c, double out[LLG_NCOEFF])
+{
+    if (!c || !out) return fail(LLG_EINVAL, "NULL argument");
+    llg::Derived d;
+    llg_status s = derived_of(c, &d);
+    if (s != LLG_OK) return s;
+    const double v[LLG_NCOEFF] = {d.zeta, d.A, d.K, d.Ms, d.alpha, d.a, d.V, d.g0, d.g1, d.ag1,
+                                  d.c_ex, d.c_an, d.sigma, d.H_start_Am, d.slope_Am, d.m_rescale};
+    std::memcpy(out, v, sizeof v);
+    return LLG_OK;
+}
+
+llg_status llg_sample_fields(const llg_ctx *c, double *H_Oe)
+{
+    if (!c || !H_Oe) return fail(LLG_EINVAL, "NULL argument");
+    llg::Derived d;
+    llg_status s = derived_of(c, &d);
+    if (s != LLG_OK) return s;
+    for (long long k = 0; k < d.n_samples; ++k) {
+        const long long n = k * d.sample_every;
+        if (d.n_half <= 0) {
+            H_Oe[k] = c->sw.H_start_Oe;
+            continue;
+        }
+        const long long ph = n % (2 * d.n_half);
+        const long long tri = ph <= d.n_half ? ph : 2 * d.n_half - ph;
+        H_Oe[k] = c->sw.H_start_Oe + (c->sw.H_turn_Oe - c->sw.H_start_Oe) * ((double)tri / (double)d.n_half);
+    }
+    return LLG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,478 @@
+// k_rod.cu -- the resident engine: whole rods live in shared memory for an entire launch of
+// thousands of Heun steps of Eq. 1, and only the sampled M(H) values reach HBM.
+//
+// Two kernels, chosen by rod size:
+//
+//  rod_twophase_kernel  (rods whose state and predictor state both fit: b >= 2 in the paper's
+//      ladder).  Several rods per CTA, each padded with a zero ghost layer so the 6-neighbour
+//      stencil has no branches.  Per step: every thread draws the thermal field of its cells,
+//      computes the predictor into the P buffer and keeps m + dt/2 f(m) and the thermal field in
+//      registers; barrier; the corrector reads P and overwrites M; barrier.
+//
+//  rod_pipelined_kernel (the b = 1 rod, 8x24x56 = 10752 cells: M alone is 129 KB, M and a full
+//      predictor copy do not fit).  One rod per CTA.  Each thread owns rows along x (fixed y, z);
+//      the CTA sweeps the x planes in lock step, computing the predictor at plane x and the
+//      corrector at plane x-1 in the same iteration, so only two planes of predictor state are
+//      ever needed (double-buffered by the parity of the plane counter).  The x-neighbours come
+//      from registers, the y- and z-neighbours from shared memory.  When nx >= 3 the corrector of
+//      the last plane of step n shares its iteration with the predictor of plane 0 of step n+1,
+//      so every iteration does both halves of the work: nx barriers per step.
+//
+// Both kernels add the neighbours in the order x-, x+, y-, y+, z-, z+ with exact zeros for
+// missing ones and use the same physics.cuh arithmetic as the plain engine, so all engines
+// produce bitwise-identical trajectories.  Samples use the canonical warp reduction (reduce.cuh).
+#include <algorithm>
+
+#include "llg_internal.h"
+#include "physics.cuh"
+#include "reduce.cuh"
+
+namespace llg {
+namespace {
+
+// At most 768 threads per CTA leaves 85 registers per thread, enough for the per-cell Heun
+// state (predictor accumulator and thermal field) of two cells or rows without spilling.
+constexpr int kMaxThreads = 768;
+
+__device__ __forceinline__ float3 zero3() { return make_float3(0.f, 0.f, 0.f); }
+
+// ------------------------------------------------------------------------------------------
+// two-phase kernel
+// ------------------------------------------------------------------------------------------
+template <int CPT>
+__global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, float *__restrict__ m_glob,
+                                                            int n_real, int rods_per_cta,
+                                                            long long step0, long long n_steps,
+                                                            float *__restrict__ samples,
+                                                            int *__restrict__ status)
+{
+    extern __shared__ float sm[];
+    const int px = p.nx + 2, py = p.ny + 2;
+    const int sy = px, sz = px * py;
+    const int rod_pad = sz * (p.nz + 2);
+    const int rod0 = blockIdx.x * rods_per_cta;
+    const int nrod = min(rods_per_cta, n_real - rod0);
+    const int tot = rods_per_cta * rod_pad;
+    float *Mx = sm, *My = Mx + tot, *Mz = My + tot;
+    float *Px = Mz + tot, *Py = Px + tot, *Pz = Py + tot;
+    const int T = blockDim.x;
+    const int ncell = p.ncells;
+    const int cta_cells = nrod * ncell;
+
+    for (int i = threadIdx.x; i < 6 * tot; i += T) sm[i] = 0.f;
+    __syncthreads();
+    for (int i = threadIdx.x; i < cta_cells; i += T) {
+        const int rod = i / ncell, c = i - rod * ncell;
+        const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
+        const int q = rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1);
+        const float *g = m_glob + ((size_t)(rod0 + rod) * ncell + c) * 3;
+        Mx[q] = g[0];
+        My[q] = g[1];
+        Mz[q] = g[2];
+    }
+
+    int pidx[CPT];
+    uint32_t cell[CPT], real[CPT];
+    bool act[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        const int i = threadIdx.x + k * T;
+        act[k] = i < cta_cells;
+        const int ii = act[k] ? i : 0;
+        const int rod = ii / ncell, c = ii - rod * ncell;
+        const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
+        pidx[k] = rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1);
+        cell[k] = (uint32_t)c;
+        real[k] = p.real0 + (uint32_t)(rod0 + rod);
+    }
+    __syncthreads();
+
+    Triangle field;
+    field.init(step0, p.n_half, p.H0, p.slope);
+    float Hn = field.value();
+    const long long se = p.sample_every;
+    long long next_sample = (samples && se > 0) ? (step0 / se + 1) * se : -1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = T >> 5;
+
+    for (long long s = 0; s < n_steps; ++s) {
+        const unsigned long long n = (unsigned long long)(step0 + s);
+        field.inc();
+        const float Hn1 = field.value();
+        float3 acc[CPT], hth[CPT];
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            if (!act[k]) continue;
+            const int q = pidx[k];
+            hth[k] = thermal_field(p.seed, real[k], cell[k], n, p.sigma);
+            const float3 mi = make_float3(Mx[q], My[q], Mz[q]);
+            float3 nb = add3(make_float3(Mx[q - 1], My[q - 1], Mz[q - 1]),
+                             make_float3(Mx[q + 1], My[q + 1], Mz[q + 1]));
+            nb = add3(nb, make_float3(Mx[q - sy], My[q - sy], Mz[q - sy]));
+            nb = add3(nb, make_float3(Mx[q + sy], My[q + sy], Mz[q + sy]));
+            nb = add3(nb, make_float3(Mx[q - sz], My[q - sz], Mz[q - sz]));
+            nb = add3(nb, make_float3(Mx[q + sz], My[q + sz], Mz[q + sz]));
+            const float3 H = effective_field(nb, mi, hth[k], p.c_ex, p.c_an, Hn);
+            const float3 s0 = llg_torque(mi, H, p.alpha);
+            const float3 mt = normalised(axpy(p.neg_dt_g1, s0, mi));
+            Px[q] = mt.x;
+            Py[q] = mt.y;
+            Pz[q] = mt.z;
+            acc[k] = axpy(p.neg_hdt_g1, s0, mi);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            if (!act[k]) continue;
+            const int q = pidx[k];
+            const float3 ti = make_float3(Px[q], Py[q], Pz[q]);
+            float3 nb = add3(make_float3(Px[q - 1], Py[q - 1], Pz[q - 1]),
+                             make_float3(Px[q + 1], Py[q + 1], Pz[q + 1]));
+            nb = add3(nb, make_float3(Px[q - sy], Py[q - sy], Pz[q - sy]));
+            nb = add3(nb, make_float3(Px[q + sy], Py[q + sy], Pz[q + sy]));
+            nb = add3(nb, make_float3(Px[q - sz], Py[q - sz], Pz[q - sz]));
+            nb = add3(nb, make_float3(Px[q + sz], Py[q + sz], Pz[q + sz]));
+            const float3 H = effective_field(nb, ti, hth[k], p.c_ex, p.c_an, Hn1);
+            const float3 s1 = llg_torque(ti, H, p.alpha);
+            const float3 mn = normalised(axpy(p.neg_hdt_g1, s1, acc[k]));
+            Mx[q] = mn.x;
+            My[q] = mn.y;
+            Mz[q] = mn.z;
+        }
+        __syncthreads();
+        Hn = Hn1;
+        if ((long long)n + 1 == next_sample) {
+            // M now holds the state after step n; the next phase only reads M until the
+            // barrier that precedes its next write, so no extra barrier is needed here.
+            const long long k = next_sample / se;
+            if (k < p.n_samples) {
+                for (int rod = warp; rod < nrod; rod += nwarps) {
+                    float part = 0.f;
+                    for (int c = lane; c < ncell; c += 32) {
+                        const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
+                        part += Mz[rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1)];
+                    }
+                    const float mean = warp_cell_mean(part, ncell);
+                    if (lane == 0) {
+                        samples[(size_t)(rod0 + rod) * p.n_samples + k] = mean;
+                        if (!isfinite(mean)) atomicOr(status, 1);
+                    }
+                }
+            }
+            next_sample += se;
+        }
+    }
+
+    for (int i = threadIdx.x; i < cta_cells; i += T) {
+        const int rod = i / ncell, c = i - rod * ncell;
+        const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
+        const int q = rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1);
+        float *g = m_glob + ((size_t)(rod0 + rod) * ncell + c) * 3;
+        g[0] = Mx[q];
+        g[1] = My[q];
+        g[2] = Mz[q];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// plane-pipelined kernel
+// ------------------------------------------------------------------------------------------
+// Shared memory: M[3][nx][PL] (state) and S[2][3][PL] (predictor planes), PL = (nz + 2) * ny:
+// each plane holds the rows (y, z) at offset q = (z + 1) * ny + y, with zero ghost lines at
+// z = -1 and z = nz; the y faces are handled by 0/1 weights.
+template <int R>
+__global__ void __launch_bounds__(kMaxThreads, 1) rod_pipelined_kernel(KParams p, float *__restrict__ m_glob,
+                                                               long long step0, long long n_steps,
+                                                               float *__restrict__ samples,
+                                                               int *__restrict__ status)
+{
+    extern __shared__ float sm[];
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int rows = ny * nz;
+    const int PL = (nz + 2) * ny;
+    float *M = sm;
+    float *S = sm + 3 * nx * PL;
+    const int T = blockDim.x;
+    const int rod = blockIdx.x;
+    const int ncell = p.ncells;
+
+    for (int i = threadIdx.x; i < 3 * nx * PL + 6 * PL; i += T) sm[i] = 0.f;
+    __syncthreads();
+    {
+        const float *g = m_glob + (size_t)rod * ncell * 3;
+        for (int c = threadIdx.x; c < ncell; c += T) {
+            const int x = c % nx, rr = c / nx;
+            const int q = ny + rr;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) M[(k * nx + x) * PL + q] = g[3 * (size_t)c + k];
+        }
+    }
+
+    int q[R];
+    float wm[R], wp[R];
+    bool act[R];
+    uint32_t cbase[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int r = threadIdx.x + j * T;
+        act[j] = r < rows;
+        const int rr = act[j] ? r : 0;
+        const int y = rr % ny;
+        q[j] = ny + rr;
+        wm[j] = y > 0 ? 1.f : 0.f;
+        wp[j] = y < ny - 1 ? 1.f : 0.f;
+        cbase[j] = (uint32_t)(rr * nx);  // cell index x + nx * (y + ny * z), rr = y + ny * z
+    }
+    const uint32_t realkey = p.real0 + (uint32_t)rod;
+
+    float3 mprev[R], mcur[R], mta[R], mtb[R], acc[R], hth[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        mprev[j] = mcur[j] = mta[j] = mtb[j] = acc[j] = hth[j] = zero3();
+    }
+    __syncthreads();
+
+    const bool merged = nx >= 3;
+    bool pa = n_steps > 0, ca = false;
+    long long sp = 0, sc = 0;
+    int xp = 0, xc = 0;
+    Triangle fpred, fcorr;
+    fpred.init(step0, p.n_half, p.H0, p.slope);
+    fcorr.init(step0 + 1, p.n_half, p.H0, p.slope);
+    float Hp = fpred.value(), Hc = fcorr.value();
+    const long long se = p.sample_every;
+    long long next_sample = (samples && se > 0) ? (step0 / se + 1) * se : -1;
+    const int lane = threadIdx.x & 31;
+
+    while (pa || ca) {
+        float3 mt_new[R], acc_new[R], h_new[R];
+        if (pa) {
+            const unsigned long long n = (unsigned long long)(step0 + sp);
+            const int slot = (int)((sp * nx + xp) & 1);
+            const float *Mx = M + (0 * nx + xp) * PL;
+            const float *My = M + (1 * nx + xp) * PL;
+            const float *Mz = M + (2 * nx + xp) * PL;
+            float *Sx = S + (slot * 3 + 0) * PL, *Sy = S + (slot * 3 + 1) * PL, *Sz = S + (slot * 3 + 2) * PL;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if (!act[j]) continue;
+                const int qq = q[j];
+                if (xp == 0) {
+                    mcur[j] = make_float3(Mx[qq], My[qq], Mz[qq]);
+                    mprev[j] = zero3();
+                }
+                float3 mnext = zero3();
+                if (xp + 1 < nx)
+                    mnext = make_float3(Mx[qq + PL], My[qq + PL], Mz[qq + PL]);
+                h_new[j] = thermal_field(p.seed, realkey, cbase[j] + (uint32_t)xp, n, p.sigma);
+                float3 nb = add3(mprev[j], mnext);
+                nb = axpy(wm[j], make_float3(Mx[qq - 1], My[qq - 1], Mz[qq - 1]), nb);
+                nb = axpy(wp[j], make_float3(Mx[qq + 1], My[qq + 1], Mz[qq + 1]), nb);
+                nb = add3(nb, make_float3(Mx[qq - ny], My[qq - ny], Mz[qq - ny]));
+                nb = add3(nb, make_float3(Mx[qq + ny], My[qq + ny], Mz[qq + ny]));
+                const float3 H = effective_field(nb, mcur[j], h_new[j], p.c_ex, p.c_an, Hp);
+                const float3 s0 = llg_torque(mcur[j], H, p.alpha);
+                mt_new[j] = normalised(axpy(p.neg_dt_g1, s0, mcur[j]));
+                acc_new[j] = axpy(p.neg_hdt_g1, s0, mcur[j]);
+                Sx[qq] = mt_new[j].x;
+                Sy[qq] = mt_new[j].y;
+                Sz[qq] = mt_new[j].z;
+                mprev[j] = mcur[j];
+                mcur[j] = mnext;
+            }
+        }
+        if (ca) {
+            const int slot = (int)((sc * nx + xc) & 1);
+            const float *Sx = S + (slot * 3 + 0) * PL, *Sy = S + (slot * 3 + 1) * PL, *Sz = S + (slot * 3 + 2) * PL;
+            float *Mx = M + (0 * nx + xc) * PL;
+            float *My = M + (1 * nx + xc) * PL;
+            float *Mz = M + (2 * nx + xc) * PL;
+            const bool has_next = xc + 1 < nx;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if (!act[j]) continue;
+                const int qq = q[j];
+                const float3 tnext = has_next ? mt_new[j] : zero3();
+                float3 nb = add3(mta[j], tnext);
+                nb = axpy(wm[j], make_float3(Sx[qq - 1], Sy[qq - 1], Sz[qq - 1]), nb);
+                nb = axpy(wp[j], make_float3(Sx[qq + 1], Sy[qq + 1], Sz[qq + 1]), nb);
+                nb = add3(nb, make_float3(Sx[qq - ny], Sy[qq - ny], Sz[qq - ny]));
+                nb = add3(nb, make_float3(Sx[qq + ny], Sy[qq + ny], Sz[qq + ny]));
+                const float3 H = effective_field(nb, mtb[j], hth[j], p.c_ex, p.c_an, Hc);
+                const float3 s1 = llg_torque(mtb[j], H, p.alpha);
+                const float3 mn = normalised(axpy(p.neg_hdt_g1, s1, acc[j]));
+                Mx[qq] = mn.x;
+                My[qq] = mn.y;
+                Mz[qq] = mn.z;
+            }
+        }
+        if (pa) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                mta[j] = xp == 0 ? zero3() : mtb[j];
+                mtb[j] = mt_new[j];
+                acc[j] = acc_new[j];
+                hth[j] = h_new[j];
+            }
+        }
+        __syncthreads();
+        if (ca && xc == nx - 1 && step0 + sc + 1 == next_sample) {
+            const long long k = next_sample / se;
+            if (k < p.n_samples && threadIdx.x < 32) {
+                float part = 0.f;
+                for (int c = lane; c < ncell; c += 32) {
+                    const int x = c % nx, rr = c / nx;
+                    part += M[(2 * nx + x) * PL + ny + rr];
+                }
+                const float mean = warp_cell_mean(part, ncell);
+                if (lane == 0) {
+                    samples[(size_t)rod * p.n_samples + k] = mean;
+                    if (!isfinite(mean)) atomicOr(status, 1);
+                }
+            }
+            next_sample += se;
+            __syncthreads();
+        }
+        // advance the schedule; the corrector takes the predictor's old position
+        const bool old_pa = pa;
+        const long long old_sp = sp;
+        const int old_xp = xp;
+        if (merged) {
+            if (pa && ++xp == nx) {
+                xp = 0;
+                ++sp;
+                fpred.inc();
+                Hp = fpred.value();
+                pa = sp < n_steps;
+            }
+        } else if (pa) {
+            if (++xp == nx) pa = false;  // one corrector-only iteration closes the step
+        } else if (ca) {
+            ++sp;
+            xp = 0;
+            fpred.inc();
+            Hp = fpred.value();
+            pa = sp < n_steps;
+        }
+        ca = old_pa;
+        if (old_pa) {
+            if (old_sp != sc) {
+                sc = old_sp;
+                fcorr.inc();
+                Hc = fcorr.value();
+            }
+            xc = old_xp;
+        }
+    }
+
+    {
+        float *g = m_glob + (size_t)rod * ncell * 3;
+        for (int c = threadIdx.x; c < ncell; c += T) {
+            const int x = c % nx, rr = c / nx;
+            const int qq = ny + rr;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) g[3 * (size_t)c + k] = M[(k * nx + x) * PL + qq];
+        }
+    }
+}
+
+int round_warp(int n) { return (n + 31) / 32 * 32; }
+
+}  // namespace
+
+bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_kind, int force_rods)
+{
+    int smem_optin = 0, nsm = 0;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return false;
+    if (p.periodic != 0) return false;  // rods have free faces
+    const size_t rod_pad = (size_t)(p.nx + 2) * (p.ny + 2) * (p.nz + 2);
+    const size_t rod_bytes = rod_pad * 6 * sizeof(float);
+    if (force_kind != 2 && rod_bytes <= (size_t)smem_optin && p.ncells <= 4 * kMaxThreads) {
+        plan->kind = 1;
+        const int cpt = p.ncells <= kMaxThreads ? 1 : (p.ncells <= 2 * kMaxThreads ? 2 : 4);
+        const int by_threads = std::max(1, kMaxThreads * cpt / p.ncells);
+        const int by_smem = (int)std::max<size_t>(1, (size_t)smem_optin / rod_bytes);
+        const int by_spread = std::max(1, (n_real + nsm - 1) / nsm);
+        int rods = std::max(1, std::min({by_threads, by_smem, by_spread}));
+        if (force_rods > 0) {
+            if (force_rods > by_threads || force_rods > by_smem) return false;
+            rods = force_rods;
+        }
+        plan->rods_per_cta = rods;
+        plan->cells_per_thread = cpt;
+        plan->threads = std::min(kMaxThreads, round_warp((rods * p.ncells + cpt - 1) / cpt));
+        plan->rows_per_thread = 0;
+        plan->smem_bytes = rods * rod_bytes;
+        plan->ctas = (n_real + rods - 1) / rods;
+        return true;
+    }
+    if (force_kind == 1) return false;
+    const size_t PL = (size_t)(p.nz + 2) * p.ny;
+    const size_t bytes = (3 * (size_t)p.nx + 6) * PL * sizeof(float);
+    const int rows = p.ny * p.nz;
+    if (bytes <= (size_t)smem_optin && rows <= 4 * kMaxThreads) {
+        plan->kind = 2;
+        const int R = rows <= kMaxThreads ? 1 : (rows <= 2 * kMaxThreads ? 2 : 4);
+        plan->rows_per_thread = R;
+        plan->threads = round_warp((rows + R - 1) / R);
+        plan->rods_per_cta = 1;
+        plan->cells_per_thread = 0;
+        plan->smem_bytes = bytes;
+        plan->ctas = n_real;
+        return true;
+    }
+    return false;
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_real,
+                        long long step0, long long n_steps, float *samples, int *status,
+                        cudaStream_t st)
+{
+    if (n_steps <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (plan.kind == 1) {
+#define LLG_TWOPHASE(C)                                                                         \
+    case C:                                                                                     \
+        e = set_smem(rod_twophase_kernel<C>, plan.smem_bytes);                                  \
+        if (e != cudaSuccess) return e;                                                         \
+        rod_twophase_kernel<C><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(               \
+            p, m, n_real, plan.rods_per_cta, step0, n_steps, samples, status);                  \
+        break;
+        switch (plan.cells_per_thread) {
+            LLG_TWOPHASE(1)
+            LLG_TWOPHASE(2)
+            LLG_TWOPHASE(4)
+            default:
+                return cudaErrorInvalidValue;
+        }
+#undef LLG_TWOPHASE
+    } else if (plan.kind == 2) {
+#define LLG_PIPELINED(R)                                                                        \
+    case R:                                                                                     \
+        e = set_smem(rod_pipelined_kernel<R>, plan.smem_bytes);                                 \
+        if (e != cudaSuccess) return e;                                                         \
+        rod_pipelined_kernel<R><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(              \
+            p, m, step0, n_steps, samples, status);                                             \
+        break;
+        switch (plan.rows_per_thread) {
+            LLG_PIPELINED(1)
+            LLG_PIPELINED(2)
+            LLG_PIPELINED(4)
+            default:
+                return cudaErrorInvalidValue;
+        }
+#undef LLG_PIPELINED
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace llg

@@ -1,0 +1,92 @@
+// llg_internal.h -- declarations shared by the host runtime (api.cpp, scaling.cpp, loops.cpp)
+// and the CUDA engines (k_plain.cu, k_rod.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace llg {
+
+// Simulation-level coefficients of one job, derived on the host in FP64 (scaling.cpp).
+struct Derived {
+    double zeta, A, K, Ms, alpha, a, V;
+    double g0, g1, ag1, c_ex, c_an, sigma;
+    double H_start_Am, H_turn_Am, slope_Am;  // slope: A/m per step of the triangle coordinate
+    long long n_half;                         // steps from H_start to H_turn (0: constant)
+    long long sample_every;                   // steps between samples
+    long long n_samples;                      // samples of one full loop
+    long long steps_per_loop;
+    double m_rescale;
+};
+
+// Per-job parameters handed to the kernels (FP32 coefficients).
+struct KParams {
+    int nx, ny, nz, ncells;
+    unsigned periodic;        // bit0 x, bit1 y, bit2 z
+    float c_ex, c_an, sigma;  // A/m
+    float neg_dt_g1;          // -dt g1   (predictor)
+    float neg_hdt_g1;         // -dt g1/2 (corrector)
+    float alpha;
+    float H0, slope;          // triangle sweep, A/m and A/m per step
+    long long n_half;
+    uint32_t seed;
+    uint32_t real0;           // key of realisation 0 of this ensemble
+    long long sample_every;   // 0: no sampling
+    long long n_samples;      // columns of the sample array
+};
+
+// Host helpers (scaling.cpp)
+double zeta_of(double b, double T, double Tc);
+// Fill d from the context's material, scaling and sweep; returns false with a message in err.
+struct MaterialIn {
+    double A0, Ms, K0, alpha, T;
+};
+struct ScalingIn {
+    int mode;
+    double Tc, delta, sK, sAlpha, sMs;
+};
+struct SweepIn {
+    double H_start_Oe, H_turn_Oe, rate_Oe_per_ns, dt, sample_dH_Oe;
+};
+bool derive(int b, double a0, const MaterialIn &m, const ScalingIn &s, const SweepIn &w, Derived *d,
+            char *err, size_t errlen);
+KParams kparams_of(const Derived &d, int nx, int ny, int nz, unsigned periodic, double dt);
+
+// ---- plain engine (k_plain.cu): state in global memory, two launches per step --------------
+// m, mt: [n_real][ncells][3]; acc, hth: same shape (scratch).
+cudaError_t plain_predictor(const KParams &p, const float *m, float *mt, float *acc, float *hth,
+                            int n_real, long long n, float Hz_n, cudaStream_t st);
+cudaError_t plain_corrector(const KParams &p, float *m, const float *mt, const float *acc,
+                            const float *hth, int n_real, float Hz_n1, cudaStream_t st);
+// samples[r][k] = mean over cells of m_z; sets *status = 1 on a non-finite mean.
+cudaError_t plain_sample(const KParams &p, const float *m, int n_real, long long k, float *samples,
+                         int *status, cudaStream_t st);
+// Host-side driver of the plain engine over n_steps from step0 (one predictor and one corrector
+// launch per step, a reduction launch per sample).
+cudaError_t plain_advance(const KParams &p, float *m, float *mt, float *acc, float *hth, int n_real,
+                          long long step0, long long n_steps, float *samples, int *status,
+                          cudaStream_t st, long long *launches);
+
+// a[r * ld + col] = v for r in [0, rows)
+cudaError_t fill_column(float *a, int rows, long long ld, long long col, float v, cudaStream_t st);
+
+// ---- resident engine (k_rod.cu): rods in shared memory for the whole launch ------------------
+struct RodPlan {
+    int kind;          // 1: two-phase (small rods, several per CTA); 2: plane-pipelined (one per CTA)
+    int rods_per_cta;  // kind 1
+    int threads;
+    int rows_per_thread;  // kind 2
+    int cells_per_thread; // kind 1
+    size_t smem_bytes;
+    int ctas;
+};
+// Choose a launch plan for n_real rods of this grid on device `dev`; returns false if no
+// resident kernel can hold the rod.
+// force_kind / force_rods: 0 = automatic.
+bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_kind = 0,
+              int force_rods = 0);
+cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_real,
+                        long long step0, long long n_steps, float *samples, int *status,
+                        cudaStream_t st);
+
+}  // namespace llg

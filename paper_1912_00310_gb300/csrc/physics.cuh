@@ -1,0 +1,125 @@
+// physics.cuh -- device arithmetic of one stochastic Heun step of Eq. 1 (FP32), shared by every
+// engine of the library: the Philox4x32-10 noise source, the Box-Muller thermal normals, the LLG
+// torque and the renormalisation.
+//
+// Eq. 1 for the unit vector m = M/Ms:  dm/dt = -g1 m x H - alpha g1 m x (m x H),
+// g1 = mu0 ge / (1 + alpha^2).  Writing s(m, H) = m x H + alpha m x (m x H), the right-hand side
+// is f = -g1 s, so the Heun predictor is m~ = normalise(m - dt g1 s(m, H_n)) and the corrector
+// m' = normalise(m - (dt g1 / 2) (s(m, H_n) + s(m~, H~_n+1))).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace llg {
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64 multiplies,
+// a half swap and a key xor, the key bumped by the Weyl constants between rounds.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Uniform in (0,1): (floor(x / 256) + 1/2) * 2^-24, exact in FP32.
+__device__ __forceinline__ float uniform24(uint32_t x)
+{
+    return fmaf(__uint2float_rn(x >> 8), 0x1p-24f, 0x1p-25f);
+}
+
+// Thermal field for (seed, realisation, cell, step): sigma times three standard normals from
+// Box-Muller on (u0, u1) and (u2, u3).  The angle is taken as 2 pi (u - 1/2), inside the
+// accurate range of the hardware sine, which negates both members of each pair.
+__device__ __forceinline__ float3 thermal_field(uint32_t seed, uint32_t real, uint32_t cell,
+                                                unsigned long long step, float sigma)
+{
+    const uint4 x = philox4x32_10(
+        make_uint4(cell, (uint32_t)step, (uint32_t)(step >> 32), 0u), seed, real);
+    const float u0 = uniform24(x.x), u1 = uniform24(x.y);
+    const float u2 = uniform24(x.z), u3 = uniform24(x.w);
+    const float kNeg2Ln2 = -1.3862943611198906f;  // -2 ln 2 : -2 ln u = -2 ln2 log2 u
+    const float v0 = fmaxf(kNeg2Ln2 * __log2f(u0), 1e-30f);
+    const float v2 = fmaxf(kNeg2Ln2 * __log2f(u2), 1e-30f);
+    const float r0 = -sigma * v0 * rsqrtf(v0);
+    const float r2 = -sigma * v2 * rsqrtf(v2);
+    const float kTwoPi = 6.283185307179586f;
+    float s1, c1;
+    __sincosf(kTwoPi * (u1 - 0.5f), &s1, &c1);
+    const float c3 = __cosf(kTwoPi * (u3 - 0.5f));
+    return make_float3(r0 * c1, r0 * s1, r2 * c3);
+}
+
+// s(m, H) = m x H + alpha m x (m x H)
+__device__ __forceinline__ float3 llg_torque(float3 m, float3 H, float alpha)
+{
+    const float ax = fmaf(m.y, H.z, -m.z * H.y);
+    const float ay = fmaf(m.z, H.x, -m.x * H.z);
+    const float az = fmaf(m.x, H.y, -m.y * H.x);
+    const float bx = fmaf(m.y, az, -m.z * ay);
+    const float by = fmaf(m.z, ax, -m.x * az);
+    const float bz = fmaf(m.x, ay, -m.y * ax);
+    return make_float3(fmaf(alpha, bx, ax), fmaf(alpha, by, ay), fmaf(alpha, bz, az));
+}
+
+__device__ __forceinline__ float3 normalised(float3 v)
+{
+    const float r = rsqrtf(fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z)));
+    return make_float3(v.x * r, v.y * r, v.z * r);
+}
+
+__device__ __forceinline__ float3 axpy(float a, float3 x, float3 y)
+{
+    return make_float3(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z));
+}
+
+__device__ __forceinline__ float3 add3(float3 a, float3 b)
+{
+    return make_float3(a.x + b.x, a.y + b.y, a.z + b.z);
+}
+
+// Effective field from the neighbour sum nb = sum_j m_j: c_ex nb + h_th + (c_an m_z + Hz) z.
+__device__ __forceinline__ float3 effective_field(float3 nb, float3 m, float3 hth, float c_ex,
+                                                  float c_an, float Hz)
+{
+    return make_float3(fmaf(c_ex, nb.x, hth.x), fmaf(c_ex, nb.y, hth.y),
+                       fmaf(c_ex, nb.z, fmaf(c_an, m.z, hth.z + Hz)));
+}
+
+// Zeeman field along z of a triangle sweep, tracked by its phase in steps.
+struct Triangle {
+    long long ph;      // position in the period [0, 2 n_half)
+    long long n_half;  // 0: constant field
+    float H0, slope;   // A/m at phase 0; A/m per step of the triangle coordinate
+
+    __device__ __forceinline__ void init(long long n, long long half, float h0, float sl)
+    {
+        n_half = half;
+        H0 = h0;
+        slope = sl;
+        ph = half > 0 ? n % (2 * half) : 0;
+    }
+    __device__ __forceinline__ float value() const
+    {
+        const long long tri = ph <= n_half ? ph : 2 * n_half - ph;
+        return fmaf(slope, (float)tri, H0);
+    }
+    __device__ __forceinline__ void inc()
+    {
+        if (n_half > 0 && ++ph == 2 * n_half) ph = 0;
+    }
+};
+
+}  // namespace llg

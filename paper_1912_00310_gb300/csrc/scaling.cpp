@@ -1,0 +1,119 @@
+// scaling.cpp -- host FP64 parameter setup of one job: the coarse-graining map (Eqs. 8-13), the
+// coefficients of Eq. 1 and of the Brown thermal field, and the triangle field sweep.
+#include <cmath>
+#include <cstdio>
+
+#include "llg_internal.h"
+
+namespace llg {
+
+namespace {
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double kMu0 = 4.0e-7 * kPi;           // T m / A
+constexpr double kGammaE = 1.76e11;             // rad / (s T), Eq. 1
+constexpr double kBoltzmann = 1.380649e-23;     // J / K
+constexpr double kAmPerOe = 1000.0 / (4.0 * kPi);
+
+// Whole number of steps in x, or -1 when x is not within 1e-6 relative of one.
+long long whole_steps(double x)
+{
+    const double r = std::nearbyint(x);
+    if (!(std::fabs(x - r) <= 1e-6 * std::fmax(1.0, std::fabs(x)))) return -1;
+    return (long long)r;
+}
+}  // namespace
+
+// zeta(b) = t/b + 1 - t with t = T/Tc (text after Eq. 11).
+double zeta_of(double b, double T, double Tc)
+{
+    const double t = T / Tc;
+    return t / b + (1.0 - t);
+}
+
+bool derive(int b, double a0, const MaterialIn &mat, const ScalingIn &sc, const SweepIn &sw,
+            Derived *d, char *err, size_t errlen)
+{
+    const bool cg = sc.mode == 1 || sc.mode == 2;
+    d->zeta = cg ? zeta_of((double)b, mat.T, sc.Tc) : 1.0;
+    // Eqs. 8-9 (A(b) = zeta A0, K(b) = zeta^3 K0) and the calibration scale factors.
+    d->A = d->zeta * mat.A0;
+    d->K = d->zeta * d->zeta * d->zeta * mat.K0 * sc.sK;
+    d->Ms = mat.Ms * sc.sMs;
+    d->alpha = mat.alpha * sc.sAlpha;
+    d->a = b * a0;
+    d->V = d->a * d->a * d->a;
+    // Eq. 1 gyromagnetic factors
+    d->g0 = kMu0 * kGammaE;
+    d->g1 = d->g0 / (1.0 + d->alpha * d->alpha);
+    d->ag1 = d->alpha * d->g1;
+    // exchange (6-neighbour stencil, bond energy 2 A a (1 - m_i.m_j)) and uniaxial anisotropy
+    d->c_ex = 2.0 * d->A / (kMu0 * d->Ms * d->a * d->a);
+    d->c_an = 2.0 * d->K / (kMu0 * d->Ms);
+    // Brown thermal field: per component, per cell and step, variance
+    // 2 alpha kB T / (gamma0 mu0 Ms V dt)
+    d->sigma = mat.T > 0.0
+                   ? std::sqrt(2.0 * d->alpha * kBoltzmann * mat.T / (d->g0 * kMu0 * d->Ms * d->V * sw.dt))
+                   : 0.0;
+    // triangle sweep
+    d->H_start_Am = sw.H_start_Oe * kAmPerOe;
+    d->H_turn_Am = sw.H_turn_Oe * kAmPerOe;
+    const double span = std::fabs(sw.H_start_Oe - sw.H_turn_Oe);
+    if (sw.rate_Oe_per_ns > 0.0 && span > 0.0) {
+        const double per_step = sw.rate_Oe_per_ns * 1e9 * sw.dt;  // Oe per step
+        d->n_half = whole_steps(span / per_step);
+        if (d->n_half <= 0) {
+            std::snprintf(err, errlen, "sweep span %.9g Oe is not a whole number of %.9g Oe steps",
+                          span, per_step);
+            return false;
+        }
+        d->sample_every = whole_steps(sw.sample_dH_Oe / per_step);
+        if (d->sample_every <= 0) {
+            std::snprintf(err, errlen, "sample spacing %.9g Oe is not a whole number of %.9g Oe steps",
+                          sw.sample_dH_Oe, per_step);
+            return false;
+        }
+        d->slope_Am = (d->H_turn_Am - d->H_start_Am) / (double)d->n_half;
+        d->steps_per_loop = 2 * d->n_half;
+        if (d->steps_per_loop % d->sample_every != 0) {
+            std::snprintf(err, errlen, "a loop of %lld steps is not a whole number of samples",
+                          d->steps_per_loop);
+            return false;
+        }
+        d->n_samples = d->steps_per_loop / d->sample_every + 1;
+    } else {
+        // constant field; sample_dH counts steps
+        d->n_half = 0;
+        d->slope_Am = 0.0;
+        d->sample_every = whole_steps(sw.sample_dH_Oe);
+        if (d->sample_every <= 0) d->sample_every = 1;
+        d->steps_per_loop = 0;
+        d->n_samples = 1;
+    }
+    // Eq. 11 (mode 1) or Eq. 13 (mode 2) rescale of m back to the unscaled system
+    d->m_rescale = sc.mode == 1 ? d->zeta : (sc.mode == 2 ? sc.delta * d->zeta + (1.0 - sc.delta) : 1.0);
+    return true;
+}
+
+KParams kparams_of(const Derived &d, int nx, int ny, int nz, unsigned periodic, double dt)
+{
+    KParams p{};
+    p.nx = nx;
+    p.ny = ny;
+    p.nz = nz;
+    p.ncells = nx * ny * nz;
+    p.periodic = periodic;
+    p.c_ex = (float)d.c_ex;
+    p.c_an = (float)d.c_an;
+    p.sigma = (float)d.sigma;
+    p.neg_dt_g1 = (float)(-dt * d.g1);
+    p.neg_hdt_g1 = (float)(-0.5 * dt * d.g1);
+    p.alpha = (float)d.alpha;
+    p.H0 = (float)d.H_start_Am;
+    p.slope = (float)d.slope_Am;
+    p.n_half = d.n_half;
+    p.sample_every = d.sample_every;
+    p.n_samples = d.n_samples;
+    return p;
+}
+
+}  // namespace llg
