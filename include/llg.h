@@ -125,11 +125,16 @@ llg_status llg_set_engine(llg_ctx *ctx, int engine);
  *   LLG_TUNE_ROD_KIND      1 two-phase kernel, 2 plane-pipelined kernel
  *   LLG_TUNE_RODS_PER_CTA  rods per CTA of the two-phase kernel
  *   LLG_TUNE_CHUNK_STEPS   Heun steps per launch (default 2^20)
+ *   LLG_TUNE_ROWS_PER_THREAD  rows per thread of the plane-pipelined kernel (1..4)
+ *   LLG_TUNE_GENERIC_KERNEL   1: the runtime-size plane-pipelined kernel even where a kernel
+ *                             specialised for the plane count exists
  * The arithmetic, and so the trajectory, does not depend on these.  Errors: EINVAL (unknown
  * key, negative value); EUNSUPPORTED at the next advance if the shape cannot hold the grid. */
 #define LLG_TUNE_ROD_KIND 1
 #define LLG_TUNE_RODS_PER_CTA 2
 #define LLG_TUNE_CHUNK_STEPS 3
+#define LLG_TUNE_ROWS_PER_THREAD 4
+#define LLG_TUNE_GENERIC_KERNEL 5
 llg_status llg_set_tuning(llg_ctx *ctx, int key, int64_t value);
 
 /* ---------------------------------------------------------------------------------------- */

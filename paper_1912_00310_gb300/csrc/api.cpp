@@ -23,7 +23,7 @@ struct llg_ctx {
     llg::ScalingIn sc{1, 858.0, 0.511, 1.0, 1.0, 1.0};
     llg::SweepIn sw{};
     int engine = LLG_ENGINE_AUTO;
-    int tune_kind = 0, tune_rods = 0;
+    int tune_kind = 0, tune_rods = 0, tune_rows = 0, tune_generic = 0;
     long long chunk_steps = 1LL << 20;
     // ensemble
     int n_real = 0;
@@ -117,7 +117,8 @@ struct DeviceGuard {
 
 int resolve_engine(const llg_ctx *c, const llg::KParams &kp, int n_real, llg::RodPlan *plan)
 {
-    const bool rod_ok = llg::rod_plan(kp, n_real, c->device, plan, c->tune_kind, c->tune_rods);
+    const bool rod_ok = llg::rod_plan(kp, n_real, c->device, plan, c->tune_kind, c->tune_rods, c->tune_rows);
+    plan->generic = c->tune_generic != 0;
     switch (c->engine) {
         case LLG_ENGINE_RESIDENT:
             return rod_ok ? LLG_ENGINE_RESIDENT : -1;
@@ -265,6 +266,13 @@ llg_status llg_set_tuning(llg_ctx *c, int key, int64_t value)
         case LLG_TUNE_RODS_PER_CTA:
             if (value > 4096) return fail(LLG_EINVAL, "rods per CTA too large");
             c->tune_rods = (int)value;
+            return LLG_OK;
+        case LLG_TUNE_ROWS_PER_THREAD:
+            if (value > 4) return fail(LLG_EINVAL, "rows per thread must be 0..4");
+            c->tune_rows = (int)value;
+            return LLG_OK;
+        case LLG_TUNE_GENERIC_KERNEL:
+            c->tune_generic = value != 0;
             return LLG_OK;
         case LLG_TUNE_CHUNK_STEPS:
             c->chunk_steps = value > 0 ? value : (1LL << 20);

@@ -39,6 +39,8 @@ __device__ __forceinline__ float3 zero3() { return make_float3(0.f, 0.f, 0.f); }
 // ------------------------------------------------------------------------------------------
 // two-phase kernel
 // ------------------------------------------------------------------------------------------
+// Shared memory: M[tot] and P[tot] float4 (x, y, z, 0), tot = rods_per_cta * (nx+2)(ny+2)(nz+2):
+// each rod padded by a zero ghost layer.
 template <int CPT>
 __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, float *__restrict__ m_glob,
                                                             int n_real, int rods_per_cta,
@@ -46,29 +48,25 @@ __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, fl
                                                             float *__restrict__ samples,
                                                             int *__restrict__ status)
 {
-    extern __shared__ float sm[];
+    extern __shared__ float4 sm4[];
     const int px = p.nx + 2, py = p.ny + 2;
     const int sy = px, sz = px * py;
     const int rod_pad = sz * (p.nz + 2);
     const int rod0 = blockIdx.x * rods_per_cta;
     const int nrod = min(rods_per_cta, n_real - rod0);
     const int tot = rods_per_cta * rod_pad;
-    float *Mx = sm, *My = Mx + tot, *Mz = My + tot;
-    float *Px = Mz + tot, *Py = Px + tot, *Pz = Py + tot;
+    float4 *M = sm4, *P = sm4 + tot;
     const int T = blockDim.x;
     const int ncell = p.ncells;
     const int cta_cells = nrod * ncell;
 
-    for (int i = threadIdx.x; i < 6 * tot; i += T) sm[i] = 0.f;
+    for (int i = threadIdx.x; i < 2 * tot; i += T) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     for (int i = threadIdx.x; i < cta_cells; i += T) {
         const int rod = i / ncell, c = i - rod * ncell;
         const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
-        const int q = rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1);
         const float *g = m_glob + ((size_t)(rod0 + rod) * ncell + c) * 3;
-        Mx[q] = g[0];
-        My[q] = g[1];
-        Mz[q] = g[2];
+        M[rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1)] = make_float4(g[0], g[1], g[2], 0.f);
     }
 
     int pidx[CPT];
@@ -104,19 +102,15 @@ __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, fl
             if (!act[k]) continue;
             const int q = pidx[k];
             hth[k] = thermal_field(p.seed, real[k], cell[k], n, p.sigma);
-            const float3 mi = make_float3(Mx[q], My[q], Mz[q]);
-            float3 nb = add3(make_float3(Mx[q - 1], My[q - 1], Mz[q - 1]),
-                             make_float3(Mx[q + 1], My[q + 1], Mz[q + 1]));
-            nb = add3(nb, make_float3(Mx[q - sy], My[q - sy], Mz[q - sy]));
-            nb = add3(nb, make_float3(Mx[q + sy], My[q + sy], Mz[q + sy]));
-            nb = add3(nb, make_float3(Mx[q - sz], My[q - sz], Mz[q - sz]));
-            nb = add3(nb, make_float3(Mx[q + sz], My[q + sz], Mz[q + sz]));
+            const float3 mi = xyz(M[q]);
+            float3 nb = add3(xyz(M[q - 1]), xyz(M[q + 1]));
+            nb = add3(nb, xyz(M[q - sy]));
+            nb = add3(nb, xyz(M[q + sy]));
+            nb = add3(nb, xyz(M[q - sz]));
+            nb = add3(nb, xyz(M[q + sz]));
             const float3 H = effective_field(nb, mi, hth[k], p.c_ex, p.c_an, Hn);
             const float3 s0 = llg_torque(mi, H, p.alpha);
-            const float3 mt = normalised(axpy(p.neg_dt_g1, s0, mi));
-            Px[q] = mt.x;
-            Py[q] = mt.y;
-            Pz[q] = mt.z;
+            P[q] = pad4(normalised(axpy(p.neg_dt_g1, s0, mi)));
             acc[k] = axpy(p.neg_hdt_g1, s0, mi);
         }
         __syncthreads();
@@ -124,19 +118,15 @@ __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, fl
         for (int k = 0; k < CPT; ++k) {
             if (!act[k]) continue;
             const int q = pidx[k];
-            const float3 ti = make_float3(Px[q], Py[q], Pz[q]);
-            float3 nb = add3(make_float3(Px[q - 1], Py[q - 1], Pz[q - 1]),
-                             make_float3(Px[q + 1], Py[q + 1], Pz[q + 1]));
-            nb = add3(nb, make_float3(Px[q - sy], Py[q - sy], Pz[q - sy]));
-            nb = add3(nb, make_float3(Px[q + sy], Py[q + sy], Pz[q + sy]));
-            nb = add3(nb, make_float3(Px[q - sz], Py[q - sz], Pz[q - sz]));
-            nb = add3(nb, make_float3(Px[q + sz], Py[q + sz], Pz[q + sz]));
+            const float3 ti = xyz(P[q]);
+            float3 nb = add3(xyz(P[q - 1]), xyz(P[q + 1]));
+            nb = add3(nb, xyz(P[q - sy]));
+            nb = add3(nb, xyz(P[q + sy]));
+            nb = add3(nb, xyz(P[q - sz]));
+            nb = add3(nb, xyz(P[q + sz]));
             const float3 H = effective_field(nb, ti, hth[k], p.c_ex, p.c_an, Hn1);
             const float3 s1 = llg_torque(ti, H, p.alpha);
-            const float3 mn = normalised(axpy(p.neg_hdt_g1, s1, acc[k]));
-            Mx[q] = mn.x;
-            My[q] = mn.y;
-            Mz[q] = mn.z;
+            M[q] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[k])));
         }
         __syncthreads();
         Hn = Hn1;
@@ -149,7 +139,7 @@ __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, fl
                     float part = 0.f;
                     for (int c = lane; c < ncell; c += 32) {
                         const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
-                        part += Mz[rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1)];
+                        part += M[rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1)].z;
                     }
                     const float mean = warp_cell_mean(part, ncell);
                     if (lane == 0) {
@@ -165,45 +155,51 @@ __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, fl
     for (int i = threadIdx.x; i < cta_cells; i += T) {
         const int rod = i / ncell, c = i - rod * ncell;
         const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
-        const int q = rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1);
+        const float4 v = M[rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1)];
         float *g = m_glob + ((size_t)(rod0 + rod) * ncell + c) * 3;
-        g[0] = Mx[q];
-        g[1] = My[q];
-        g[2] = Mz[q];
+        g[0] = v.x;
+        g[1] = v.y;
+        g[2] = v.z;
     }
 }
 
 // ------------------------------------------------------------------------------------------
 // plane-pipelined kernel
 // ------------------------------------------------------------------------------------------
-// Shared memory: M[3][nx][PL] (state) and S[2][3][PL] (predictor planes), PL = (nz + 2) * ny:
-// each plane holds the rows (y, z) at offset q = (z + 1) * ny + y, with zero ghost lines at
-// z = -1 and z = nz; the y faces are handled by 0/1 weights.
+// Shared memory (float4 = x, y, z, 0): M[nx][PL] (state) and S[2][PL] (predictor planes),
+// PL = (nz + 2) * ny: each plane holds the rows (y, z) at offset q = (z + 1) * ny + y, with zero
+// ghost lines at z = -1 and z = nz; the y faces are handled by 0/1 weights.
+// Threads per CTA of the plane-pipelined kernel for R rows per thread.  The register file is split
+// over the four SM sub-partitions (16384 registers each), so the per-thread budget is set by the
+// warps per sub-partition: 768 or 672 threads -> 80 registers, 512 -> 128, 384 -> 168.
+__host__ __device__ constexpr int pipelined_max_threads(int R)
+{
+    return R == 1 ? 768 : (R == 2 ? 672 : (R == 3 ? 512 : 384));
+}
+
 template <int R>
-__global__ void __launch_bounds__(kMaxThreads, 1) rod_pipelined_kernel(KParams p, float *__restrict__ m_glob,
+__global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_kernel(KParams p, float *__restrict__ m_glob,
                                                                long long step0, long long n_steps,
                                                                float *__restrict__ samples,
                                                                int *__restrict__ status)
 {
-    extern __shared__ float sm[];
+    extern __shared__ float4 sm4[];
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int rows = ny * nz;
     const int PL = (nz + 2) * ny;
-    float *M = sm;
-    float *S = sm + 3 * nx * PL;
+    float4 *M = sm4;
+    float4 *S = sm4 + nx * PL;
     const int T = blockDim.x;
     const int rod = blockIdx.x;
     const int ncell = p.ncells;
 
-    for (int i = threadIdx.x; i < 3 * nx * PL + 6 * PL; i += T) sm[i] = 0.f;
+    for (int i = threadIdx.x; i < (nx + 2) * PL; i += T) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     {
         const float *g = m_glob + (size_t)rod * ncell * 3;
         for (int c = threadIdx.x; c < ncell; c += T) {
             const int x = c % nx, rr = c / nx;
-            const int q = ny + rr;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) M[(k * nx + x) * PL + q] = g[3 * (size_t)c + k];
+            M[x * PL + ny + rr] = make_float4(g[3 * (size_t)c], g[3 * (size_t)c + 1], g[3 * (size_t)c + 2], 0.f);
         }
     }
 
@@ -222,7 +218,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) rod_pipelined_kernel(KParams p
         wp[j] = y < ny - 1 ? 1.f : 0.f;
         cbase[j] = (uint32_t)(rr * nx);  // cell index x + nx * (y + ny * z), rr = y + ny * z
     }
-    const uint32_t realkey = p.real0 + (uint32_t)rod;
+    const PhiloxKeys keys = philox_keys(p.seed, p.real0 + (uint32_t)rod);
 
     float3 mprev[R], mcur[R], mta[R], mtb[R], acc[R], hth[R];
 #pragma unroll
@@ -247,45 +243,36 @@ __global__ void __launch_bounds__(kMaxThreads, 1) rod_pipelined_kernel(KParams p
         float3 mt_new[R], acc_new[R], h_new[R];
         if (pa) {
             const unsigned long long n = (unsigned long long)(step0 + sp);
-            const int slot = (int)((sp * nx + xp) & 1);
-            const float *Mx = M + (0 * nx + xp) * PL;
-            const float *My = M + (1 * nx + xp) * PL;
-            const float *Mz = M + (2 * nx + xp) * PL;
-            float *Sx = S + (slot * 3 + 0) * PL, *Sy = S + (slot * 3 + 1) * PL, *Sz = S + (slot * 3 + 2) * PL;
+            const float4 *Mp = M + xp * PL;
+            float4 *Sw = S + (int)((sp * nx + xp) & 1) * PL;
+            const bool has_next = xp + 1 < nx;
 #pragma unroll
             for (int j = 0; j < R; ++j) {
                 if (!act[j]) continue;
                 const int qq = q[j];
                 if (xp == 0) {
-                    mcur[j] = make_float3(Mx[qq], My[qq], Mz[qq]);
+                    mcur[j] = xyz(Mp[qq]);
                     mprev[j] = zero3();
                 }
-                float3 mnext = zero3();
-                if (xp + 1 < nx)
-                    mnext = make_float3(Mx[qq + PL], My[qq + PL], Mz[qq + PL]);
-                h_new[j] = thermal_field(p.seed, realkey, cbase[j] + (uint32_t)xp, n, p.sigma);
+                const float3 mnext = has_next ? xyz(Mp[qq + PL]) : zero3();
+                h_new[j] = thermal_field(keys, cbase[j] + (uint32_t)xp, n, p.sigma);
                 float3 nb = add3(mprev[j], mnext);
-                nb = axpy(wm[j], make_float3(Mx[qq - 1], My[qq - 1], Mz[qq - 1]), nb);
-                nb = axpy(wp[j], make_float3(Mx[qq + 1], My[qq + 1], Mz[qq + 1]), nb);
-                nb = add3(nb, make_float3(Mx[qq - ny], My[qq - ny], Mz[qq - ny]));
-                nb = add3(nb, make_float3(Mx[qq + ny], My[qq + ny], Mz[qq + ny]));
+                nb = axpy(wm[j], xyz(Mp[qq - 1]), nb);
+                nb = axpy(wp[j], xyz(Mp[qq + 1]), nb);
+                nb = add3(nb, xyz(Mp[qq - ny]));
+                nb = add3(nb, xyz(Mp[qq + ny]));
                 const float3 H = effective_field(nb, mcur[j], h_new[j], p.c_ex, p.c_an, Hp);
                 const float3 s0 = llg_torque(mcur[j], H, p.alpha);
                 mt_new[j] = normalised(axpy(p.neg_dt_g1, s0, mcur[j]));
                 acc_new[j] = axpy(p.neg_hdt_g1, s0, mcur[j]);
-                Sx[qq] = mt_new[j].x;
-                Sy[qq] = mt_new[j].y;
-                Sz[qq] = mt_new[j].z;
+                Sw[qq] = pad4(mt_new[j]);
                 mprev[j] = mcur[j];
                 mcur[j] = mnext;
             }
         }
         if (ca) {
-            const int slot = (int)((sc * nx + xc) & 1);
-            const float *Sx = S + (slot * 3 + 0) * PL, *Sy = S + (slot * 3 + 1) * PL, *Sz = S + (slot * 3 + 2) * PL;
-            float *Mx = M + (0 * nx + xc) * PL;
-            float *My = M + (1 * nx + xc) * PL;
-            float *Mz = M + (2 * nx + xc) * PL;
+            const float4 *Sr = S + (int)((sc * nx + xc) & 1) * PL;
+            float4 *Mw = M + xc * PL;
             const bool has_next = xc + 1 < nx;
 #pragma unroll
             for (int j = 0; j < R; ++j) {
@@ -293,16 +280,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) rod_pipelined_kernel(KParams p
                 const int qq = q[j];
                 const float3 tnext = has_next ? mt_new[j] : zero3();
                 float3 nb = add3(mta[j], tnext);
-                nb = axpy(wm[j], make_float3(Sx[qq - 1], Sy[qq - 1], Sz[qq - 1]), nb);
-                nb = axpy(wp[j], make_float3(Sx[qq + 1], Sy[qq + 1], Sz[qq + 1]), nb);
-                nb = add3(nb, make_float3(Sx[qq - ny], Sy[qq - ny], Sz[qq - ny]));
-                nb = add3(nb, make_float3(Sx[qq + ny], Sy[qq + ny], Sz[qq + ny]));
+                nb = axpy(wm[j], xyz(Sr[qq - 1]), nb);
+                nb = axpy(wp[j], xyz(Sr[qq + 1]), nb);
+                nb = add3(nb, xyz(Sr[qq - ny]));
+                nb = add3(nb, xyz(Sr[qq + ny]));
                 const float3 H = effective_field(nb, mtb[j], hth[j], p.c_ex, p.c_an, Hc);
                 const float3 s1 = llg_torque(mtb[j], H, p.alpha);
-                const float3 mn = normalised(axpy(p.neg_hdt_g1, s1, acc[j]));
-                Mx[qq] = mn.x;
-                My[qq] = mn.y;
-                Mz[qq] = mn.z;
+                Mw[qq] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[j])));
             }
         }
         if (pa) {
@@ -319,10 +303,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) rod_pipelined_kernel(KParams p
             const long long k = next_sample / se;
             if (k < p.n_samples && threadIdx.x < 32) {
                 float part = 0.f;
-                for (int c = lane; c < ncell; c += 32) {
-                    const int x = c % nx, rr = c / nx;
-                    part += M[(2 * nx + x) * PL + ny + rr];
-                }
+                for (int c = lane; c < ncell; c += 32) part += M[(c % nx) * PL + ny + c / nx].z;
                 const float mean = warp_cell_mean(part, ncell);
                 if (lane == 0) {
                     samples[(size_t)rod * p.n_samples + k] = mean;
@@ -367,10 +348,189 @@ __global__ void __launch_bounds__(kMaxThreads, 1) rod_pipelined_kernel(KParams p
     {
         float *g = m_glob + (size_t)rod * ncell * 3;
         for (int c = threadIdx.x; c < ncell; c += T) {
-            const int x = c % nx, rr = c / nx;
-            const int qq = ny + rr;
+            const float4 v = M[(c % nx) * PL + ny + c / nx];
+            g[3 * (size_t)c] = v.x;
+            g[3 * (size_t)c + 1] = v.y;
+            g[3 * (size_t)c + 2] = v.z;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// plane-pipelined kernel with a compile-time plane count (the b = 1 rod has NX = 8): the x sweep
+// of a step is unrolled, so the plane windows rotate by register renaming and the slot parity
+// is a constant.  Same schedule and arithmetic as rod_pipelined_kernel.
+// ------------------------------------------------------------------------------------------
+template <int R, int NX>
+__global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_kernel(
+    KParams p, float *__restrict__ m_glob, long long step0, long long n_steps,
+    float *__restrict__ samples, int *__restrict__ status)
+{
+    static_assert(NX >= 3 && NX % 2 == 0, "merged schedule with even plane count");
+    extern __shared__ float4 sm4[];
+    const int ny = p.ny, nz = p.nz;
+    const int rows = ny * nz;
+    const int PL = (nz + 2) * ny;
+    float4 *M = sm4;
+    float4 *S = sm4 + NX * PL;
+    const int T = blockDim.x;
+    const int rod = blockIdx.x;
+    const int ncell = p.ncells;
+
+    for (int i = threadIdx.x; i < (NX + 2) * PL; i += T) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    {
+        const float *g = m_glob + (size_t)rod * ncell * 3;
+        for (int c = threadIdx.x; c < ncell; c += T) {
+            const int x = c % NX, rr = c / NX;
+            M[x * PL + ny + rr] = make_float4(g[3 * (size_t)c], g[3 * (size_t)c + 1], g[3 * (size_t)c + 2], 0.f);
+        }
+    }
+
+    int q[R];
+    float wm[R], wp[R];
+    bool act[R];
+    uint32_t cbase[R];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) g[3 * (size_t)c + k] = M[(k * nx + x) * PL + qq];
+    for (int j = 0; j < R; ++j) {
+        const int r = threadIdx.x + j * T;
+        act[j] = r < rows;
+        const int rr = act[j] ? r : 0;
+        const int y = rr % ny;
+        q[j] = ny + rr;
+        wm[j] = y > 0 ? 1.f : 0.f;
+        wp[j] = y < ny - 1 ? 1.f : 0.f;
+        cbase[j] = (uint32_t)(rr * NX);
+    }
+    const PhiloxKeys keys = philox_keys(p.seed, p.real0 + (uint32_t)rod);
+    // carried per row: m(x-1), m(x) for the predictor; m~(x-2), m~(x-1), acc(x-1), h(x-1) for
+    // the corrector one plane behind
+    float3 mA[R], mB[R], tA[R], tB[R], acc[R], hth[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) mA[j] = mB[j] = tA[j] = tB[j] = acc[j] = hth[j] = zero3();
+    __syncthreads();
+
+    Triangle field;
+    field.init(step0, p.n_half, p.H0, p.slope);
+    float Hs = field.value();  // field at step s
+    field.inc();
+    float Hs1 = field.value();  // field at step s + 1
+    float Hprev = Hs;           // field at step s (the end of step s - 1), for its corrector
+    const long long se = p.sample_every;
+    long long next_sample = (samples && se > 0) ? (step0 / se + 1) * se : -1;
+    const int lane = threadIdx.x & 31;
+
+    auto sample_if_due = [&](long long done) {
+        if (done != next_sample) return;
+        const long long k = next_sample / se;
+        if (k < p.n_samples && threadIdx.x < 32) {
+            float part = 0.f;
+            for (int c = lane; c < ncell; c += 32) part += M[(c % NX) * PL + ny + c / NX].z;
+            const float mean = warp_cell_mean(part, ncell);
+            if (lane == 0) {
+                samples[(size_t)rod * p.n_samples + k] = mean;
+                if (!isfinite(mean)) atomicOr(status, 1);
+            }
+        }
+        next_sample += se;
+        __syncthreads();
+    };
+
+    for (long long s = 0; s < n_steps; ++s) {
+        const unsigned long long n = (unsigned long long)(step0 + s);
+#pragma unroll
+        for (int x = 0; x < NX; ++x) {
+            // ---- predictor at (s, x): writes slot x & 1 ----
+            const float4 *Mp = M + x * PL;
+            float4 *Sw = S + (x & 1) * PL;
+            float3 tnew[R], anew[R], hnew[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if (!act[j]) continue;
+                const int qq = q[j];
+                if (x == 0) {
+                    mA[j] = zero3();
+                    mB[j] = xyz(Mp[qq]);
+                }
+                const float3 mnext = x + 1 < NX ? xyz(Mp[qq + PL]) : zero3();
+                hnew[j] = thermal_field(keys, cbase[j] + (uint32_t)x, n, p.sigma);
+                float3 nb = add3(mA[j], mnext);
+                nb = axpy(wm[j], xyz(Mp[qq - 1]), nb);
+                nb = axpy(wp[j], xyz(Mp[qq + 1]), nb);
+                nb = add3(nb, xyz(Mp[qq - ny]));
+                nb = add3(nb, xyz(Mp[qq + ny]));
+                const float3 H = effective_field(nb, mB[j], hnew[j], p.c_ex, p.c_an, Hs);
+                const float3 s0 = llg_torque(mB[j], H, p.alpha);
+                tnew[j] = normalised(axpy(p.neg_dt_g1, s0, mB[j]));
+                anew[j] = axpy(p.neg_hdt_g1, s0, mB[j]);
+                Sw[qq] = pad4(tnew[j]);
+                mA[j] = mB[j];
+                mB[j] = mnext;
+            }
+            // ---- corrector one plane behind: (s, x-1), or (s-1, NX-1) at x = 0 ----
+            if (x > 0 || s > 0) {
+                const int xc = x > 0 ? x - 1 : NX - 1;
+                const float4 *Sr = S + (xc & 1) * PL;
+                float4 *Mw = M + xc * PL;
+                const float Hc = x > 0 ? Hs1 : Hprev;
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    if (!act[j]) continue;
+                    const int qq = q[j];
+                    const float3 tnext = x > 0 ? tnew[j] : zero3();
+                    float3 nb = add3(tA[j], tnext);
+                    nb = axpy(wm[j], xyz(Sr[qq - 1]), nb);
+                    nb = axpy(wp[j], xyz(Sr[qq + 1]), nb);
+                    nb = add3(nb, xyz(Sr[qq - ny]));
+                    nb = add3(nb, xyz(Sr[qq + ny]));
+                    const float3 H = effective_field(nb, tB[j], hth[j], p.c_ex, p.c_an, Hc);
+                    const float3 s1 = llg_torque(tB[j], H, p.alpha);
+                    Mw[qq] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[j])));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                tA[j] = x == 0 ? zero3() : tB[j];
+                tB[j] = tnew[j];
+                acc[j] = anew[j];
+                hth[j] = hnew[j];
+            }
+            __syncthreads();
+            if (x == 0 && s > 0) sample_if_due(step0 + s);
+        }
+        Hprev = Hs1;
+        Hs = Hs1;
+        field.inc();
+        Hs1 = field.value();
+    }
+    if (n_steps > 0) {
+        // the corrector of the last plane of the last step
+        const float4 *Sr = S + ((NX - 1) & 1) * PL;
+        float4 *Mw = M + (NX - 1) * PL;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (!act[j]) continue;
+            const int qq = q[j];
+            float3 nb = tA[j];
+            nb = axpy(wm[j], xyz(Sr[qq - 1]), nb);
+            nb = axpy(wp[j], xyz(Sr[qq + 1]), nb);
+            nb = add3(nb, xyz(Sr[qq - ny]));
+            nb = add3(nb, xyz(Sr[qq + ny]));
+            const float3 H = effective_field(nb, tB[j], hth[j], p.c_ex, p.c_an, Hprev);
+            const float3 s1 = llg_torque(tB[j], H, p.alpha);
+            Mw[qq] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[j])));
+        }
+        __syncthreads();
+        sample_if_due(step0 + n_steps);
+    }
+
+    {
+        float *g = m_glob + (size_t)rod * ncell * 3;
+        for (int c = threadIdx.x; c < ncell; c += T) {
+            const float4 v = M[(c % NX) * PL + ny + c / NX];
+            g[3 * (size_t)c] = v.x;
+            g[3 * (size_t)c + 1] = v.y;
+            g[3 * (size_t)c + 2] = v.z;
         }
     }
 }
@@ -379,7 +539,8 @@ int round_warp(int n) { return (n + 31) / 32 * 32; }
 
 }  // namespace
 
-bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_kind, int force_rods)
+bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_kind, int force_rods,
+              int force_rows)
 {
     int smem_optin = 0, nsm = 0;
     if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
@@ -387,7 +548,7 @@ bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_ki
         return false;
     if (p.periodic != 0) return false;  // rods have free faces
     const size_t rod_pad = (size_t)(p.nx + 2) * (p.ny + 2) * (p.nz + 2);
-    const size_t rod_bytes = rod_pad * 6 * sizeof(float);
+    const size_t rod_bytes = rod_pad * 2 * sizeof(float4);
     if (force_kind != 2 && rod_bytes <= (size_t)smem_optin && p.ncells <= 4 * kMaxThreads) {
         plan->kind = 1;
         const int cpt = p.ncells <= kMaxThreads ? 1 : (p.ncells <= 2 * kMaxThreads ? 2 : 4);
@@ -409,20 +570,23 @@ bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_ki
     }
     if (force_kind == 1) return false;
     const size_t PL = (size_t)(p.nz + 2) * p.ny;
-    const size_t bytes = (3 * (size_t)p.nx + 6) * PL * sizeof(float);
+    const size_t bytes = ((size_t)p.nx + 2) * PL * sizeof(float4);
     const int rows = p.ny * p.nz;
-    if (bytes <= (size_t)smem_optin && rows <= 4 * kMaxThreads) {
-        plan->kind = 2;
-        const int R = rows <= kMaxThreads ? 1 : (rows <= 2 * kMaxThreads ? 2 : 4);
-        plan->rows_per_thread = R;
-        plan->threads = round_warp((rows + R - 1) / R);
-        plan->rods_per_cta = 1;
-        plan->cells_per_thread = 0;
-        plan->smem_bytes = bytes;
-        plan->ctas = n_real;
-        return true;
+    if (bytes > (size_t)smem_optin) return false;
+    int R = force_rows;
+    if (R == 0) {
+        // fewest rows per thread that fit; three rows per thread for the b = 1 rod (1344 rows)
+        R = rows <= 768 ? 1 : (rows <= 1536 ? 3 : 4);
     }
-    return false;
+    if (R < 1 || R > 4 || (rows + R - 1) / R > pipelined_max_threads(R)) return false;
+    plan->kind = 2;
+    plan->rows_per_thread = R;
+    plan->threads = round_warp((rows + R - 1) / R);
+    plan->rods_per_cta = 1;
+    plan->cells_per_thread = 0;
+    plan->smem_bytes = bytes;
+    plan->ctas = n_real;
+    return true;
 }
 
 template <typename K>
@@ -456,14 +620,22 @@ cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_r
     } else if (plan.kind == 2) {
 #define LLG_PIPELINED(R)                                                                        \
     case R:                                                                                     \
-        e = set_smem(rod_pipelined_kernel<R>, plan.smem_bytes);                                 \
-        if (e != cudaSuccess) return e;                                                         \
-        rod_pipelined_kernel<R><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(              \
-            p, m, step0, n_steps, samples, status);                                             \
+        if (p.nx == 8 && !plan.generic) {                                                       \
+            e = set_smem(rod_pipelined_nx_kernel<R, 8>, plan.smem_bytes);                       \
+            if (e != cudaSuccess) return e;                                                     \
+            rod_pipelined_nx_kernel<R, 8><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(    \
+                p, m, step0, n_steps, samples, status);                                         \
+        } else {                                                                                \
+            e = set_smem(rod_pipelined_kernel<R>, plan.smem_bytes);                             \
+            if (e != cudaSuccess) return e;                                                     \
+            rod_pipelined_kernel<R><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(          \
+                p, m, step0, n_steps, samples, status);                                         \
+        }                                                                                       \
         break;
         switch (plan.rows_per_thread) {
             LLG_PIPELINED(1)
             LLG_PIPELINED(2)
+            LLG_PIPELINED(3)
             LLG_PIPELINED(4)
             default:
                 return cudaErrorInvalidValue;

@@ -79,12 +79,13 @@ struct RodPlan {
     int cells_per_thread; // kind 1
     size_t smem_bytes;
     int ctas;
+    bool generic = false;  // kind 2: use the runtime-nx kernel even where a specialised one exists
 };
 // Choose a launch plan for n_real rods of this grid on device `dev`; returns false if no
 // resident kernel can hold the rod.
 // force_kind / force_rods: 0 = automatic.
 bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_kind = 0,
-              int force_rods = 0);
+              int force_rods = 0, int force_rows = 0);
 cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_real,
                         long long step0, long long n_steps, float *samples, int *status,
                         cudaStream_t st);

@@ -17,20 +17,52 @@ namespace llg {
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64 multiplies,
 // a half swap and a key xor, the key bumped by the Weyl constants between rounds.
 // ------------------------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1)
+{
+    const unsigned long long p0 = (unsigned long long)kPhiloxM0 * c.x;
+    const unsigned long long p1 = (unsigned long long)kPhiloxM1 * c.z;
+    return make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1,
+                      (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+}
+
+// Key bumped round by round (for keys that differ between the cells of a thread).
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         if (r > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
+            k0 += kPhiloxW0;
+            k1 += kPhiloxW1;
         }
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        c = philox_round(c, k0, k1);
     }
+    return c;
+}
+
+// The ten round keys of one key, computed once (for a key shared by all cells of a CTA, where
+// they stay in uniform registers across the step loop).
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1)
+{
+    PhiloxKeys K;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        K.k0[r] = k0 + (uint32_t)r * kPhiloxW0;
+        K.k1[r] = k1 + (uint32_t)r * kPhiloxW1;
+    }
+    return K;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys &K)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) c = philox_round(c, K.k0[r], K.k1[r]);
     return c;
 }
 
@@ -40,14 +72,12 @@ __device__ __forceinline__ float uniform24(uint32_t x)
     return fmaf(__uint2float_rn(x >> 8), 0x1p-24f, 0x1p-25f);
 }
 
-// Thermal field for (seed, realisation, cell, step): sigma times three standard normals from
-// Box-Muller on (u0, u1) and (u2, u3).  The angle is taken as 2 pi (u - 1/2), inside the
-// accurate range of the hardware sine, which negates both members of each pair.
-__device__ __forceinline__ float3 thermal_field(uint32_t seed, uint32_t real, uint32_t cell,
-                                                unsigned long long step, float sigma)
+// Thermal field from the four Philox words of (seed, realisation, cell, step): sigma times
+// three standard normals from Box-Muller on (u0, u1) and (u2, u3).  The angle is taken as
+// 2 pi (u - 1/2), inside the accurate range of the hardware sine, which negates both members of
+// each pair.
+__device__ __forceinline__ float3 box_muller3(uint4 x, float sigma)
 {
-    const uint4 x = philox4x32_10(
-        make_uint4(cell, (uint32_t)step, (uint32_t)(step >> 32), 0u), seed, real);
     const float u0 = uniform24(x.x), u1 = uniform24(x.y);
     const float u2 = uniform24(x.z), u3 = uniform24(x.w);
     const float kNeg2Ln2 = -1.3862943611198906f;  // -2 ln 2 : -2 ln u = -2 ln2 log2 u
@@ -60,6 +90,23 @@ __device__ __forceinline__ float3 thermal_field(uint32_t seed, uint32_t real, ui
     __sincosf(kTwoPi * (u1 - 0.5f), &s1, &c1);
     const float c3 = __cosf(kTwoPi * (u3 - 0.5f));
     return make_float3(r0 * c1, r0 * s1, r2 * c3);
+}
+
+__device__ __forceinline__ uint4 noise_counter(uint32_t cell, unsigned long long step)
+{
+    return make_uint4(cell, (uint32_t)step, (uint32_t)(step >> 32), 0u);
+}
+
+__device__ __forceinline__ float3 thermal_field(uint32_t seed, uint32_t real, uint32_t cell,
+                                                unsigned long long step, float sigma)
+{
+    return box_muller3(philox4x32_10(noise_counter(cell, step), seed, real), sigma);
+}
+
+__device__ __forceinline__ float3 thermal_field(const PhiloxKeys &K, uint32_t cell,
+                                                unsigned long long step, float sigma)
+{
+    return box_muller3(philox4x32_10(noise_counter(cell, step), K), sigma);
 }
 
 // s(m, H) = m x H + alpha m x (m x H)
@@ -89,6 +136,9 @@ __device__ __forceinline__ float3 add3(float3 a, float3 b)
 {
     return make_float3(a.x + b.x, a.y + b.y, a.z + b.z);
 }
+
+__device__ __forceinline__ float3 xyz(float4 v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float4 pad4(float3 v) { return make_float4(v.x, v.y, v.z, 0.f); }
 
 // Effective field from the neighbour sum nb = sum_j m_j: c_ex nb + h_th + (c_an m_z + Hz) z.
 __device__ __forceinline__ float3 effective_field(float3 nb, float3 m, float3 hth, float c_ex,

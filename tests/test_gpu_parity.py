@@ -129,6 +129,28 @@ def test_engines_bitwise_equal(pkg, dims, b, n_real):
         assert torch.equal(sm[:, 1:4], outs[0][1][:, 1:4])
 
 
+def test_b1_kernel_variants_bitwise_equal(pkg):
+    """The b = 1 rod: the plane-count-specialised kernel and the runtime-size kernel, with 2, 3
+    and 4 rows per thread, give bitwise-equal states and samples over several sample intervals."""
+    dims, b, dt, n_real = ROD_DIMS[1], 1, 2e-15, 3
+    outs = []
+    for generic in (0, 1):
+        for rows in (2, 3, 4):
+            g = make_grid(pkg, dims, b, dt, engine=pkg.ENGINE_RESIDENT, rate=10000.0)
+            g.set_tuning(pkg.TUNE_GENERIC_KERNEL, generic)
+            g.set_tuning(pkg.TUNE_ROWS_PER_THREAD, rows)
+            g.reset(seed=5, n_real=n_real)
+            S = torch.full((n_real, g.n_samples), float("nan"), device="cuda")
+            g.advance(2 * g.sample_every + 13, S)
+            g.advance(g.sample_every - 13, S)
+            outs.append((state_of(g, n_real), S[:, :4].clone()))
+            g.close()
+    assert not torch.isnan(outs[0][1][:, 1:4]).any()
+    for st, sm in outs[1:]:
+        assert torch.equal(st, outs[0][0])
+        assert torch.equal(sm[:, 1:4], outs[0][1][:, 1:4])
+
+
 def test_samples_match_oracle(pkg, orc):
     """A short loop (+-5 Oe at 1000 Oe/ns, 1 Oe spacing): every sample against the oracle."""
     dims, b, dt, n_real = ROD_DIMS[4], 4, 10e-15, 4
