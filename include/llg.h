@@ -128,6 +128,8 @@ llg_status llg_set_engine(llg_ctx *ctx, int engine);
  *   LLG_TUNE_ROWS_PER_THREAD  rows per thread of the plane-pipelined kernel (1..4)
  *   LLG_TUNE_GENERIC_KERNEL   1: the runtime-size plane-pipelined kernel even where a kernel
  *                             specialised for the plane count exists
+ *   LLG_TUNE_BALANCE          0: one rod per CTA even when the rods do not fill whole waves
+ *                             (default 1: rod-steps balanced over a co-resident grid)
  * The arithmetic, and so the trajectory, does not depend on these.  Errors: EINVAL (unknown
  * key, negative value); EUNSUPPORTED at the next advance if the shape cannot hold the grid. */
 #define LLG_TUNE_ROD_KIND 1
@@ -135,6 +137,7 @@ llg_status llg_set_engine(llg_ctx *ctx, int engine);
 #define LLG_TUNE_CHUNK_STEPS 3
 #define LLG_TUNE_ROWS_PER_THREAD 4
 #define LLG_TUNE_GENERIC_KERNEL 5
+#define LLG_TUNE_BALANCE 6
 llg_status llg_set_tuning(llg_ctx *ctx, int key, int64_t value);
 
 /* ---------------------------------------------------------------------------------------- */

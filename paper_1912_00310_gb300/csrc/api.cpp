@@ -23,7 +23,7 @@ struct llg_ctx {
     llg::ScalingIn sc{1, 858.0, 0.511, 1.0, 1.0, 1.0};
     llg::SweepIn sw{};
     int engine = LLG_ENGINE_AUTO;
-    int tune_kind = 0, tune_rods = 0, tune_rows = 0, tune_generic = 0;
+    int tune_kind = 0, tune_rods = 0, tune_rows = 0, tune_generic = 0, tune_balance = 1;
     long long chunk_steps = 1LL << 20;
     // ensemble
     int n_real = 0;
@@ -36,6 +36,8 @@ struct llg_ctx {
     float *d_samples = nullptr;  // staging for host sample buffers
     size_t samples_cap = 0;
     int *d_status = nullptr;
+    unsigned *d_flags = nullptr;  // resident engine: hand-off flags of the balanced schedule
+    size_t flags_cap = 0;
     long long launches = 0;
 };
 
@@ -119,6 +121,7 @@ int resolve_engine(const llg_ctx *c, const llg::KParams &kp, int n_real, llg::Ro
 {
     const bool rod_ok = llg::rod_plan(kp, n_real, c->device, plan, c->tune_kind, c->tune_rods, c->tune_rows);
     plan->generic = c->tune_generic != 0;
+    plan->balance = c->tune_balance != 0;
     switch (c->engine) {
         case LLG_ENGINE_RESIDENT:
             return rod_ok ? LLG_ENGINE_RESIDENT : -1;
@@ -174,7 +177,7 @@ llg_status llg_create_grid(llg_ctx **out, int nx, int ny, int nz, double a0_m, i
 void llg_destroy(llg_ctx *c)
 {
     if (!c) return;
-    if (!c->d_status && !c->d_m) {  // nothing was ever put on the device
+    if (!c->d_status && !c->d_m && !c->d_flags) {  // nothing was ever put on the device
         delete c;
         return;
     }
@@ -184,6 +187,7 @@ void llg_destroy(llg_ctx *c)
     cudaFree(c->d_scratch);
     cudaFree(c->d_samples);
     cudaFree(c->d_status);
+    cudaFree(c->d_flags);
     cudaGetLastError();
     delete c;
 }
@@ -274,7 +278,11 @@ llg_status llg_set_tuning(llg_ctx *c, int key, int64_t value)
         case LLG_TUNE_GENERIC_KERNEL:
             c->tune_generic = value != 0;
             return LLG_OK;
+        case LLG_TUNE_BALANCE:
+            c->tune_balance = value != 0;
+            return LLG_OK;
         case LLG_TUNE_CHUNK_STEPS:
+            if (value > (1LL << 30)) return fail(LLG_EINVAL, "at most 2^30 steps per launch");
             c->chunk_steps = value > 0 ? value : (1LL << 20);
             return LLG_OK;
         default:
@@ -322,11 +330,18 @@ llg_status llg_advance(llg_ctx *c, int64_t n_steps, float *m_samples)
     const int eng = resolve_engine(c, kp, c->n_real, &plan);
     if (eng < 0) return fail(LLG_EUNSUPPORTED, "the selected engine cannot hold a %dx%dx%d grid", c->nx, c->ny, c->nz);
     if (eng == LLG_ENGINE_RESIDENT) {
+        if (c->flags_cap < (size_t)c->n_real) {
+            cudaFree(c->d_flags);
+            c->d_flags = nullptr;
+            c->flags_cap = 0;
+            LLG_CUDA(cudaMalloc(&c->d_flags, sizeof(unsigned) * (size_t)c->n_real), "cudaMalloc(flags)");
+            c->flags_cap = (size_t)c->n_real;
+        }
         const long long chunk = c->chunk_steps;
         for (long long done = 0; done < n_steps; done += chunk) {
             const long long k = n_steps - done < chunk ? n_steps - done : chunk;
             LLG_CUDA(llg::rod_advance(kp, plan, c->d_m, c->n_real, c->step + done, k, m_samples,
-                                      c->d_status, c->stream),
+                                      c->d_status, c->d_flags, c->stream),
                      "resident engine launch");
             ++c->launches;
         }
@@ -361,6 +376,7 @@ llg_status llg_sync(llg_ctx *c, double timeout_s)
     int st = 0;
     if (!c->d_status) return LLG_OK;
     LLG_CUDA(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+    if (st & 2) return fail(LLG_ETIMEOUT, "a resident-engine hand-off wait gave up");
     if (st) return fail(LLG_ENONFINITE, "a non-finite magnetisation was sampled");
     return LLG_OK;
 }

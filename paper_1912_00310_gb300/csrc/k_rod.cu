@@ -22,6 +22,7 @@
 // missing ones and use the same physics.cuh arithmetic as the plain engine, so all engines
 // produce bitwise-identical trajectories.  Samples use the canonical warp reduction (reduce.cuh).
 #include <algorithm>
+#include <cstring>
 
 #include "llg_internal.h"
 #include "physics.cuh"
@@ -362,68 +363,42 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_ker
 // is a constant.  Same schedule and arithmetic as rod_pipelined_kernel.
 // ------------------------------------------------------------------------------------------
 template <int R, int NX>
-__global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_kernel(
-    KParams p, float *__restrict__ m_glob, long long step0, long long n_steps,
-    float *__restrict__ samples, int *__restrict__ status)
-{
-    static_assert(NX >= 3 && NX % 2 == 0, "merged schedule with even plane count");
-    extern __shared__ float4 sm4[];
-    const int ny = p.ny, nz = p.nz;
-    const int rows = ny * nz;
-    const int PL = (nz + 2) * ny;
-    float4 *M = sm4;
-    float4 *S = sm4 + NX * PL;
-    const int T = blockDim.x;
-    const int rod = blockIdx.x;
-    const int ncell = p.ncells;
-
-    for (int i = threadIdx.x; i < (NX + 2) * PL; i += T) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
-    {
-        const float *g = m_glob + (size_t)rod * ncell * 3;
-        for (int c = threadIdx.x; c < ncell; c += T) {
-            const int x = c % NX, rr = c / NX;
-            M[x * PL + ny + rr] = make_float4(g[3 * (size_t)c], g[3 * (size_t)c + 1], g[3 * (size_t)c + 2], 0.f);
-        }
-    }
-
+struct PipelinedRod {
+    float4 *M, *S;
+    int ny, PL, ncell;
     int q[R];
     float wm[R], wp[R];
     bool act[R];
     uint32_t cbase[R];
+
+    __device__ void setup(float4 *sm, const KParams &p)
+    {
+        ny = p.ny;
+        PL = (p.nz + 2) * ny;
+        ncell = p.ncells;
+        M = sm;
+        S = sm + NX * PL;
+        const int rows = ny * p.nz;
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-        const int r = threadIdx.x + j * T;
-        act[j] = r < rows;
-        const int rr = act[j] ? r : 0;
-        const int y = rr % ny;
-        q[j] = ny + rr;
-        wm[j] = y > 0 ? 1.f : 0.f;
-        wp[j] = y < ny - 1 ? 1.f : 0.f;
-        cbase[j] = (uint32_t)(rr * NX);
+        for (int j = 0; j < R; ++j) {
+            const int r = threadIdx.x + j * blockDim.x;
+            act[j] = r < rows;
+            const int rr = act[j] ? r : 0;
+            const int y = rr % ny;
+            q[j] = ny + rr;
+            wm[j] = y > 0 ? 1.f : 0.f;
+            wp[j] = y < ny - 1 ? 1.f : 0.f;
+            cbase[j] = (uint32_t)(rr * NX);
+        }
     }
-    const PhiloxKeys keys = philox_keys(p.seed, p.real0 + (uint32_t)rod);
-    // carried per row: m(x-1), m(x) for the predictor; m~(x-2), m~(x-1), acc(x-1), h(x-1) for
-    // the corrector one plane behind
-    float3 mA[R], mB[R], tA[R], tB[R], acc[R], hth[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) mA[j] = mB[j] = tA[j] = tB[j] = acc[j] = hth[j] = zero3();
-    __syncthreads();
 
-    Triangle field;
-    field.init(step0, p.n_half, p.H0, p.slope);
-    float Hs = field.value();  // field at step s
-    field.inc();
-    float Hs1 = field.value();  // field at step s + 1
-    float Hprev = Hs;           // field at step s (the end of step s - 1), for its corrector
-    const long long se = p.sample_every;
-    long long next_sample = (samples && se > 0) ? (step0 / se + 1) * se : -1;
-    const int lane = threadIdx.x & 31;
-
-    auto sample_if_due = [&](long long done) {
-        if (done != next_sample) return;
-        const long long k = next_sample / se;
+    // Sample k of rod `rod`: the canonical warp reduction of m_z over the cells in M, then a
+    // barrier (the next iteration overwrites plane 0).
+    __device__ __forceinline__ void sample(const KParams &p, int rod, long long k, float *__restrict__ samples,
+                                        int *__restrict__ status)
+    {
         if (k < p.n_samples && threadIdx.x < 32) {
+            const int lane = threadIdx.x;
             float part = 0.f;
             for (int c = lane; c < ncell; c += 32) part += M[(c % NX) * PL + ny + c / NX].z;
             const float mean = warp_cell_mean(part, ncell);
@@ -432,105 +407,217 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_
                 if (!isfinite(mean)) atomicOr(status, 1);
             }
         }
-        next_sample += se;
         __syncthreads();
-    };
+    }
 
-    for (long long s = 0; s < n_steps; ++s) {
-        const unsigned long long n = (unsigned long long)(step0 + s);
+    // Load rod `rod` from global memory (L2, bypassing L1: another SM may have written it during
+    // this launch), advance it from step s0 by ns steps, store it back.
+    __device__ __forceinline__ void run(const KParams &p, float *__restrict__ m_glob, int rod, long long s0,
+                                        long long ns, float *__restrict__ samples, int *__restrict__ status)
+    {
+        {
+            const float *g = m_glob + (size_t)rod * ncell * 3;
+            for (int c = threadIdx.x; c < ncell; c += blockDim.x)
+                M[(c % NX) * PL + ny + c / NX] = make_float4(__ldcg(g + 3 * (size_t)c), __ldcg(g + 3 * (size_t)c + 1),
+                                                             __ldcg(g + 3 * (size_t)c + 2), 0.f);
+        }
+        const PhiloxKeys keys = philox_keys(p.seed, p.real0 + (uint32_t)rod);
+        // carried per row: m(x-1), m(x) for the predictor; m~(x-2), m~(x-1), acc(x-1), h(x-1)
+        // for the corrector one plane behind
+        float3 mA[R], mB[R], tA[R], tB[R], acc[R], hth[R];
 #pragma unroll
-        for (int x = 0; x < NX; ++x) {
-            // ---- predictor at (s, x): writes slot x & 1 ----
-            const float4 *Mp = M + x * PL;
-            float4 *Sw = S + (x & 1) * PL;
-            float3 tnew[R], anew[R], hnew[R];
+        for (int j = 0; j < R; ++j) mA[j] = mB[j] = tA[j] = tB[j] = acc[j] = hth[j] = zero3();
+        __syncthreads();
+
+        Triangle field;
+        field.init(s0, p.n_half, p.H0, p.slope);
+        float Hs = field.value();  // field at step s
+        field.inc();
+        float Hs1 = field.value();  // field at step s + 1
+        float Hprev = Hs;           // field at step s (the end of step s - 1), for its corrector
+        const long long se = p.sample_every;
+        long long next_sample = (samples && se > 0) ? (s0 / se + 1) * se : -1;
+
+        for (long long s = 0; s < ns; ++s) {
+            const unsigned long long n = (unsigned long long)(s0 + s);
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                if (!act[j]) continue;
-                const int qq = q[j];
-                if (x == 0) {
-                    mA[j] = zero3();
-                    mB[j] = xyz(Mp[qq]);
-                }
-                const float3 mnext = x + 1 < NX ? xyz(Mp[qq + PL]) : zero3();
-                hnew[j] = thermal_field(keys, cbase[j] + (uint32_t)x, n, p.sigma);
-                float3 nb = add3(mA[j], mnext);
-                nb = axpy(wm[j], xyz(Mp[qq - 1]), nb);
-                nb = axpy(wp[j], xyz(Mp[qq + 1]), nb);
-                nb = add3(nb, xyz(Mp[qq - ny]));
-                nb = add3(nb, xyz(Mp[qq + ny]));
-                const float3 H = effective_field(nb, mB[j], hnew[j], p.c_ex, p.c_an, Hs);
-                const float3 s0 = llg_torque(mB[j], H, p.alpha);
-                tnew[j] = normalised(axpy(p.neg_dt_g1, s0, mB[j]));
-                anew[j] = axpy(p.neg_hdt_g1, s0, mB[j]);
-                Sw[qq] = pad4(tnew[j]);
-                mA[j] = mB[j];
-                mB[j] = mnext;
-            }
-            // ---- corrector one plane behind: (s, x-1), or (s-1, NX-1) at x = 0 ----
-            if (x > 0 || s > 0) {
-                const int xc = x > 0 ? x - 1 : NX - 1;
-                const float4 *Sr = S + (xc & 1) * PL;
-                float4 *Mw = M + xc * PL;
-                const float Hc = x > 0 ? Hs1 : Hprev;
+            for (int x = 0; x < NX; ++x) {
+                // ---- predictor at (s, x): writes slot x & 1 ----
+                const float4 *Mp = M + x * PL;
+                float4 *Sw = S + (x & 1) * PL;
+                float3 tnew[R], anew[R], hnew[R];
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
                     if (!act[j]) continue;
                     const int qq = q[j];
-                    const float3 tnext = x > 0 ? tnew[j] : zero3();
-                    float3 nb = add3(tA[j], tnext);
-                    nb = axpy(wm[j], xyz(Sr[qq - 1]), nb);
-                    nb = axpy(wp[j], xyz(Sr[qq + 1]), nb);
-                    nb = add3(nb, xyz(Sr[qq - ny]));
-                    nb = add3(nb, xyz(Sr[qq + ny]));
-                    const float3 H = effective_field(nb, tB[j], hth[j], p.c_ex, p.c_an, Hc);
-                    const float3 s1 = llg_torque(tB[j], H, p.alpha);
-                    Mw[qq] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[j])));
+                    if (x == 0) {
+                        mA[j] = zero3();
+                        mB[j] = xyz(Mp[qq]);
+                    }
+                    const float3 mnext = x + 1 < NX ? xyz(Mp[qq + PL]) : zero3();
+                    hnew[j] = thermal_field(keys, cbase[j] + (uint32_t)x, n, p.sigma);
+                    float3 nb = add3(mA[j], mnext);
+                    nb = axpy(wm[j], xyz(Mp[qq - 1]), nb);
+                    nb = axpy(wp[j], xyz(Mp[qq + 1]), nb);
+                    nb = add3(nb, xyz(Mp[qq - ny]));
+                    nb = add3(nb, xyz(Mp[qq + ny]));
+                    const float3 H = effective_field(nb, mB[j], hnew[j], p.c_ex, p.c_an, Hs);
+                    const float3 s0v = llg_torque(mB[j], H, p.alpha);
+                    tnew[j] = normalised(axpy(p.neg_dt_g1, s0v, mB[j]));
+                    anew[j] = axpy(p.neg_hdt_g1, s0v, mB[j]);
+                    Sw[qq] = pad4(tnew[j]);
+                    mA[j] = mB[j];
+                    mB[j] = mnext;
+                }
+                // ---- corrector one plane behind: (s, x-1), or (s-1, NX-1) at x = 0 ----
+                if (x > 0 || s > 0) {
+                    const int xc = x > 0 ? x - 1 : NX - 1;
+                    const float4 *Sr = S + (xc & 1) * PL;
+                    float4 *Mw = M + xc * PL;
+                    const float Hc = x > 0 ? Hs1 : Hprev;
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        if (!act[j]) continue;
+                        const int qq = q[j];
+                        const float3 tnext = x > 0 ? tnew[j] : zero3();
+                        float3 nb = add3(tA[j], tnext);
+                        nb = axpy(wm[j], xyz(Sr[qq - 1]), nb);
+                        nb = axpy(wp[j], xyz(Sr[qq + 1]), nb);
+                        nb = add3(nb, xyz(Sr[qq - ny]));
+                        nb = add3(nb, xyz(Sr[qq + ny]));
+                        const float3 H = effective_field(nb, tB[j], hth[j], p.c_ex, p.c_an, Hc);
+                        const float3 s1 = llg_torque(tB[j], H, p.alpha);
+                        Mw[qq] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[j])));
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    tA[j] = x == 0 ? zero3() : tB[j];
+                    tB[j] = tnew[j];
+                    acc[j] = anew[j];
+                    hth[j] = hnew[j];
+                }
+                __syncthreads();
+                if (x == 0 && s > 0 && s0 + s == next_sample) {
+                    sample(p, rod, next_sample / se, samples, status);
+                    next_sample += se;
                 }
             }
+            Hprev = Hs1;
+            Hs = Hs1;
+            field.inc();
+            Hs1 = field.value();
+        }
+        if (ns > 0) {
+            // the corrector of the last plane of the last step
+            const float4 *Sr = S + ((NX - 1) & 1) * PL;
+            float4 *Mw = M + (NX - 1) * PL;
 #pragma unroll
             for (int j = 0; j < R; ++j) {
-                tA[j] = x == 0 ? zero3() : tB[j];
-                tB[j] = tnew[j];
-                acc[j] = anew[j];
-                hth[j] = hnew[j];
+                if (!act[j]) continue;
+                const int qq = q[j];
+                float3 nb = tA[j];
+                nb = axpy(wm[j], xyz(Sr[qq - 1]), nb);
+                nb = axpy(wp[j], xyz(Sr[qq + 1]), nb);
+                nb = add3(nb, xyz(Sr[qq - ny]));
+                nb = add3(nb, xyz(Sr[qq + ny]));
+                const float3 H = effective_field(nb, tB[j], hth[j], p.c_ex, p.c_an, Hprev);
+                const float3 s1 = llg_torque(tB[j], H, p.alpha);
+                Mw[qq] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[j])));
             }
             __syncthreads();
-            if (x == 0 && s > 0) sample_if_due(step0 + s);
+            if (s0 + ns == next_sample) sample(p, rod, next_sample / se, samples, status);
         }
-        Hprev = Hs1;
-        Hs = Hs1;
-        field.inc();
-        Hs1 = field.value();
-    }
-    if (n_steps > 0) {
-        // the corrector of the last plane of the last step
-        const float4 *Sr = S + ((NX - 1) & 1) * PL;
-        float4 *Mw = M + (NX - 1) * PL;
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-            if (!act[j]) continue;
-            const int qq = q[j];
-            float3 nb = tA[j];
-            nb = axpy(wm[j], xyz(Sr[qq - 1]), nb);
-            nb = axpy(wp[j], xyz(Sr[qq + 1]), nb);
-            nb = add3(nb, xyz(Sr[qq - ny]));
-            nb = add3(nb, xyz(Sr[qq + ny]));
-            const float3 H = effective_field(nb, tB[j], hth[j], p.c_ex, p.c_an, Hprev);
-            const float3 s1 = llg_torque(tB[j], H, p.alpha);
-            Mw[qq] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[j])));
+        {
+            float *g = m_glob + (size_t)rod * ncell * 3;
+            for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+                const float4 v = M[(c % NX) * PL + ny + c / NX];
+                g[3 * (size_t)c] = v.x;
+                g[3 * (size_t)c + 1] = v.y;
+                g[3 * (size_t)c + 2] = v.z;
+            }
         }
         __syncthreads();
-        sample_if_due(step0 + n_steps);
     }
+};
 
-    {
-        float *g = m_glob + (size_t)rod * ncell * 3;
-        for (int c = threadIdx.x; c < ncell; c += T) {
-            const float4 v = M[(c % NX) * PL + ny + c / NX];
-            g[3 * (size_t)c] = v.x;
-            g[3 * (size_t)c + 1] = v.y;
-            g[3 * (size_t)c + 2] = v.z;
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Longest a CTA waits for the first part of a rod it finishes before giving up (the producer
+// normally finished long before: it ran the first part at the start of its own schedule).
+constexpr unsigned long long kHandoffTimeoutNs = 30ull * 1000 * 1000 * 1000;
+
+// Balanced schedule of one launch: up to three segments per CTA {rod, first step offset, steps,
+// kind}, kind 0 = whole rod or plain part, 1 = first part (signal flags[rod] when done),
+// 2 = last part (wait for flags[rod] first).  Built on the host (McNaughton's wrap-around rule:
+// all n_real * n_steps rod-steps laid end to end and cut into gridDim.x equal slices; a rod cut at
+// a slice boundary runs its first steps at the start of the next CTA's slice and its last steps
+// at the end of this CTA's slice).  Passed as a kernel parameter so the segment fields are
+// uniform (constant-bank) values.
+constexpr int kMaxBalancedCtas = 256;
+struct BalancedSchedule {
+    int4 seg[3 * kMaxBalancedCtas];
+};
+
+// balanced == 0: one rod per CTA over [step0, step0 + n_steps).
+// balanced == 1: the segments of `sched`; needs all CTAs co-resident (cooperative launch).
+template <int R, int NX>
+__global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_kernel(
+    KParams p, float *__restrict__ m_glob, long long step0, int n_steps, float *__restrict__ samples,
+    int *__restrict__ status, unsigned *__restrict__ flags, int balanced,
+    const __grid_constant__ BalancedSchedule sched)
+{
+    static_assert(NX >= 3 && NX % 2 == 0, "merged schedule with even plane count");
+    extern __shared__ float4 sm4[];
+    const int PL = (p.nz + 2) * p.ny;
+    for (int i = threadIdx.x; i < (NX + 2) * PL; i += blockDim.x) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    PipelinedRod<R, NX> w;
+    w.setup(sm4, p);
+    __syncthreads();
+    __shared__ int go;
+    const int nseg = balanced ? 3 : 1;
+    for (int i = 0; i < nseg; ++i) {
+        const int4 sg = balanced ? sched.seg[3 * blockIdx.x + i] : make_int4(blockIdx.x, 0, n_steps, 0);
+        if (sg.z <= 0) continue;
+        if (sg.w == 2) {
+            if (threadIdx.x == 0) {
+                const unsigned long long t0 = globaltimer_ns();
+                int ok = 1;
+                while (ld_acquire_gpu(flags + sg.x) == 0u) {
+                    if (globaltimer_ns() - t0 > kHandoffTimeoutNs) {
+                        ok = 0;
+                        atomicOr(status, 2);
+                        break;
+                    }
+                    __nanosleep(200);
+                }
+                __threadfence();
+                go = ok;
+            }
+            __syncthreads();
+            if (!go) break;
+        }
+        w.run(p, m_glob, sg.x, step0 + sg.y, sg.z, samples, status);
+        if (sg.w == 1 && threadIdx.x == 0) {
+            __threadfence();
+            st_release_gpu(flags + sg.x, 1u);
         }
     }
 }
@@ -595,9 +682,73 @@ static cudaError_t set_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Launch of the nx-specialised kernel: balanced over a co-resident grid when the rods do not
+// divide evenly into waves, else one rod per CTA.
+// McNaughton's wrap-around schedule of n_real rods x N steps over G co-resident CTAs.
+static void balanced_schedule(int n_real, int N, int G, BalancedSchedule *sc)
+{
+    std::memset(sc, 0, sizeof *sc);
+    const long long W = (long long)n_real * N;
+    const long long C = (W + G - 1) / G;
+    for (int j = 0; j < G; ++j) {
+        const long long lo = std::min((long long)j * C, W), hi = std::min(lo + C, W);
+        int k = 0;
+        for (long long pos = lo; pos < hi && k < 3;) {
+            const long long rod = pos / N, off = pos - rod * N;
+            const long long len = std::min(hi, (rod + 1) * N) - pos;
+            int4 &g = sc->seg[3 * j + k++];
+            g.x = (int)rod;
+            g.z = (int)len;
+            if (off != 0) {  // first len steps, then hand off
+                g.y = 0;
+                g.w = 1;
+            } else if (len < N) {  // last len steps, after the hand-off
+                g.y = (int)(N - len);
+                g.w = 2;
+            } else {
+                g.y = 0;
+                g.w = 0;
+            }
+            pos += len;
+        }
+    }
+}
+
+// Launch of the nx-specialised kernel: balanced over a co-resident grid when the rods do not
+// divide evenly into waves, else one rod per CTA.
+template <int R, int NX>
+static cudaError_t launch_nx(const KParams &p, const RodPlan &plan, float *m, int n_real, long long step0,
+                             long long n_steps, float *samples, int *status, unsigned *flags,
+                             cudaStream_t st)
+{
+    auto kern = rod_pipelined_nx_kernel<R, NX>;
+    cudaError_t e = set_smem(kern, plan.smem_bytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, plan.threads, plan.smem_bytes)) != cudaSuccess)
+        return e;
+    const int resident = nsm * per_sm;
+    BalancedSchedule sched;  // kernel parameter (copied at launch)
+    int ns = (int)n_steps;
+    if (plan.balance && flags && resident > 0 && resident <= kMaxBalancedCtas && n_real > resident &&
+        n_real % resident != 0) {
+        balanced_schedule(n_real, ns, resident, &sched);
+        if ((e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)n_real, st)) != cudaSuccess) return e;
+        int balanced = 1;
+        void *args[] = {(void *)&p, (void *)&m, (void *)&step0, (void *)&ns, (void *)&samples,
+                        (void *)&status, (void *)&flags, (void *)&balanced, (void *)&sched};
+        return cudaLaunchCooperativeKernel((const void *)kern, dim3(resident), dim3(plan.threads), args,
+                                           plan.smem_bytes, st);
+    }
+    kern<<<n_real, plan.threads, plan.smem_bytes, st>>>(p, m, step0, ns, samples, status, flags, 0, sched);
+    return cudaGetLastError();
+}
+
 cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_real,
                         long long step0, long long n_steps, float *samples, int *status,
-                        cudaStream_t st)
+                        unsigned *flags, cudaStream_t st)
 {
     if (n_steps <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
@@ -621,10 +772,7 @@ cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_r
 #define LLG_PIPELINED(R)                                                                        \
     case R:                                                                                     \
         if (p.nx == 8 && !plan.generic) {                                                       \
-            e = set_smem(rod_pipelined_nx_kernel<R, 8>, plan.smem_bytes);                       \
-            if (e != cudaSuccess) return e;                                                     \
-            rod_pipelined_nx_kernel<R, 8><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(    \
-                p, m, step0, n_steps, samples, status);                                         \
+            e = launch_nx<R, 8>(p, plan, m, n_real, step0, n_steps, samples, status, flags, st); \
         } else {                                                                                \
             e = set_smem(rod_pipelined_kernel<R>, plan.smem_bytes);                             \
             if (e != cudaSuccess) return e;                                                     \

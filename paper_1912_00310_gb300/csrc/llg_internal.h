@@ -80,14 +80,17 @@ struct RodPlan {
     size_t smem_bytes;
     int ctas;
     bool generic = false;  // kind 2: use the runtime-nx kernel even where a specialised one exists
+    bool balance = true;   // kind 2: balance rod-steps over a co-resident grid (needs flags)
 };
 // Choose a launch plan for n_real rods of this grid on device `dev`; returns false if no
 // resident kernel can hold the rod.
 // force_kind / force_rods: 0 = automatic.
 bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_kind = 0,
               int force_rods = 0, int force_rows = 0);
+// flags: n_real words of device scratch for the balanced schedule's hand-offs (may be NULL:
+// then no balancing).  status bit 0: non-finite sample; bit 1: a hand-off wait gave up.
 cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_real,
                         long long step0, long long n_steps, float *samples, int *status,
-                        cudaStream_t st);
+                        unsigned *flags, cudaStream_t st);
 
 }  // namespace llg

@@ -151,6 +151,29 @@ def test_b1_kernel_variants_bitwise_equal(pkg):
         assert torch.equal(sm[:, 1:4], outs[0][1][:, 1:4])
 
 
+@pytest.mark.parametrize("n_real,steps", [(160, 2 * 50 + 7), (2 * 152 + 5, 50), (155, 3)])
+def test_balanced_schedule_is_bitwise_equal(pkg, n_real, steps):
+    """More b = 1 rods than one wave: the balanced schedule (rods split between CTAs at step
+    boundaries, hand-off through global memory) gives the same states and samples as one rod
+    per CTA."""
+    dims, b, dt = ROD_DIMS[1], 1, 2e-15
+    outs = []
+    for balance in (0, 1):
+        g = make_grid(pkg, dims, b, dt, engine=pkg.ENGINE_RESIDENT, rate=1e5, sample_dH=1.0)
+        g.set_tuning(pkg.TUNE_BALANCE, balance)
+        g.reset(seed=8, n_real=n_real)
+        assert g.sample_every == 5
+        S = torch.full((n_real, g.n_samples), float("nan"), device="cuda")
+        g.advance(steps, S)
+        g.advance(steps, S)
+        outs.append((state_of(g, n_real), S.clone()))
+        g.close()
+    assert torch.equal(outs[0][0], outs[1][0])
+    k = (2 * steps) // 5
+    assert not torch.isnan(outs[0][1][:, 1:k + 1]).any()
+    assert torch.equal(outs[0][1][:, 1:k + 1], outs[1][1][:, 1:k + 1])
+
+
 def test_samples_match_oracle(pkg, orc):
     """A short loop (+-5 Oe at 1000 Oe/ns, 1 Oe spacing): every sample against the oracle."""
     dims, b, dt, n_real = ROD_DIMS[4], 4, 10e-15, 4
