@@ -211,6 +211,38 @@ llg_status llg_loop_stats_host(const float *m_samples, int n_real, int64_t n_sam
                                const double *H_Oe, int64_t k_turn, int mode, double zeta,
                                double delta, llg_loop_stats *out, double *mean_out);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Allocation-free advance (no counterpart in the paper)                                     */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Largest n_real * ncells that llg_plain_advance_noalloc accepts.  Its scratch (9 floats per
+ * cell-realisation plus a 256-byte header, about 9.4 MB) is a fixed array inside the library
+ * that every GPU which loads the library holds until the process exits. */
+#define LLG_NOALLOC_MAX_CELL_REALISATIONS 262144
+
+/* The plain engine (a predictor and a corrector launch per Heun step, as llg_advance with
+ * LLG_ENGINE_PLAIN) for callers that cannot allocate device memory: code running while its
+ * stream is captured into a CUDA graph, programs whose device memory belongs to an allocator
+ * that must account for every byte, and loops that cannot accept the device synchronisation a
+ * cudaMalloc may cause.  It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * lives in the library's fixed device array described above, and the context is used only for
+ * its host-side parameters (grid, material, scaling, sweep; its own device buffers are untouched).
+ *   m          device [n_real][ncells][3], the state, advanced in place from step index step0
+ *   seed, real_offset  noise keys (seed, real_offset + r) as in llg_reset
+ *   m_samples  device [n_real][llg_num_samples] or NULL, written as llg_advance does
+ *   cuda_stream  stream for the work; the call is asynchronous unless status_out is given
+ *   status_out host or NULL: when given, the call waits for the stream and stores 1 if a
+ *              non-finite sample was seen, else 0
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture begins.  All calls share
+ * the one array and the status word is cleared at the start of each call, so calls whose GPU work
+ * overlaps (other streams, other host threads) race and must be serialised by the caller.
+ * Errors: EINVAL (n_real * ncells above LLG_NOALLOC_MAX_CELL_REALISATIONS, bad arguments, setup
+ * incomplete), ECUDA. */
+llg_status llg_plain_advance_noalloc(const llg_ctx *ctx, float *m, int n_real, uint32_t seed,
+                                     uint32_t real_offset, int64_t step0, int64_t n_steps,
+                                     float *m_samples, void *cuda_stream, int *status_out);
+
 #ifdef __cplusplus
 }
 #endif

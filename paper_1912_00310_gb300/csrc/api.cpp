@@ -136,6 +136,19 @@ int resolve_engine(const llg_ctx *c, const llg::KParams &kp, int n_real, llg::Ro
 
 }  // namespace
 
+namespace llg {
+void set_last_error(const char *msg) { std::snprintf(g_err, sizeof g_err, "%s", msg); }
+
+llg_status kparams_from_ctx(const llg_ctx *c, KParams *out)
+{
+    Derived d;
+    const llg_status s = derived_of(c, &d);
+    if (s != LLG_OK) return s;
+    *out = kparams_of(d, c->nx, c->ny, c->nz, c->periodic, c->sw.dt);
+    return LLG_OK;
+}
+}  // namespace llg
+
 extern "C" {
 
 const char *llg_last_error(void) { return g_err; }

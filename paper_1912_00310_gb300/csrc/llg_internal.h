@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/llg.h"
+
 namespace llg {
 
 // Simulation-level coefficients of one job, derived on the host in FP64 (scaling.cpp).
@@ -93,4 +95,13 @@ cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_r
                         long long step0, long long n_steps, float *samples, int *status,
                         unsigned *flags, cudaStream_t st);
 
+// ---- host runtime helpers (api.cpp) ---------------------------------------------------------
+// Store a message for llg_last_error() on this thread.
+void set_last_error(const char *msg);
+}  // namespace llg
+
+namespace llg {
+// Kernel parameters of a context's grid, material, scaling and sweep (host-side derivation
+// only; seed and real0 are left zero).  Returns LLG_OK or the setup error (message stored).
+llg_status kparams_from_ctx(const llg_ctx *ctx, KParams *out);
 }  // namespace llg
