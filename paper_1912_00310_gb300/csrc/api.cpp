@@ -38,6 +38,8 @@ struct llg_ctx {
     int *d_status = nullptr;
     unsigned *d_flags = nullptr;  // resident engine: hand-off flags of the balanced schedule
     size_t flags_cap = 0;
+    float *d_slab = nullptr;      // streaming engine: two float4 ping-pong buffers + partial sums
+    size_t slab_cap = 0;          // floats
     long long launches = 0;
 };
 
@@ -117,20 +119,23 @@ struct DeviceGuard {
     }
 };
 
-int resolve_engine(const llg_ctx *c, const llg::KParams &kp, int n_real, llg::RodPlan *plan)
+int resolve_engine(const llg_ctx *c, const llg::KParams &kp, int n_real, llg::RodPlan *plan,
+                   llg::SlabPlan *splan)
 {
     const bool rod_ok = llg::rod_plan(kp, n_real, c->device, plan, c->tune_kind, c->tune_rods, c->tune_rows);
     plan->generic = c->tune_generic != 0;
     plan->balance = c->tune_balance != 0;
+    llg::SlabPlan tmp;
+    const bool slab_ok = llg::slab_plan(kp, c->device, splan ? splan : &tmp);
     switch (c->engine) {
         case LLG_ENGINE_RESIDENT:
             return rod_ok ? LLG_ENGINE_RESIDENT : -1;
         case LLG_ENGINE_PLAIN:
             return LLG_ENGINE_PLAIN;
         case LLG_ENGINE_STREAM:
-            return -1;
+            return slab_ok ? LLG_ENGINE_STREAM : -1;
         default:
-            return rod_ok ? LLG_ENGINE_RESIDENT : LLG_ENGINE_PLAIN;
+            return rod_ok ? LLG_ENGINE_RESIDENT : (slab_ok ? LLG_ENGINE_STREAM : LLG_ENGINE_PLAIN);
     }
 }
 
@@ -201,6 +206,7 @@ void llg_destroy(llg_ctx *c)
     cudaFree(c->d_samples);
     cudaFree(c->d_status);
     cudaFree(c->d_flags);
+    cudaFree(c->d_slab);
     cudaGetLastError();
     delete c;
 }
@@ -340,7 +346,8 @@ llg_status llg_advance(llg_ctx *c, int64_t n_steps, float *m_samples)
     kp.seed = c->seed;
     kp.real0 = c->real0;
     llg::RodPlan plan{};
-    const int eng = resolve_engine(c, kp, c->n_real, &plan);
+    llg::SlabPlan splan{};
+    const int eng = resolve_engine(c, kp, c->n_real, &plan, &splan);
     if (eng < 0) return fail(LLG_EUNSUPPORTED, "the selected engine cannot hold a %dx%dx%d grid", c->nx, c->ny, c->nz);
     if (eng == LLG_ENGINE_RESIDENT) {
         if (c->flags_cap < (size_t)c->n_real) {
@@ -358,6 +365,16 @@ llg_status llg_advance(llg_ctx *c, int64_t n_steps, float *m_samples)
                      "resident engine launch");
             ++c->launches;
         }
+    } else if (eng == LLG_ENGINE_STREAM) {
+        const size_t cells = (size_t)c->n_real * (size_t)ncells_of(c);
+        const size_t need = 8 * cells + llg::slab_partial_floats(c->n_real);
+        s = grow(&c->d_slab, &c->slab_cap, need);
+        if (s != LLG_OK) return s;
+        float4 *a = reinterpret_cast<float4 *>(c->d_slab);
+        float4 *b = a + cells;
+        LLG_CUDA(llg::slab_advance(kp, splan, c->d_m, c->n_real, c->step, n_steps, m_samples, c->d_status, a, b,
+                                   c->d_slab + 8 * cells, c->stream, &c->launches),
+                 "streaming engine launch");
     } else {
         const size_t per = (size_t)c->n_real * (size_t)ncells_of(c) * 3;
         s = grow(&c->d_scratch, &c->scratch_cap, 3 * per);
@@ -504,7 +521,7 @@ int llg_active_engine(const llg_ctx *c)
     if (!c || derived_of(c, &d) != LLG_OK) return -1;
     llg::KParams kp = llg::kparams_of(d, c->nx, c->ny, c->nz, c->periodic, c->sw.dt);
     llg::RodPlan plan{};
-    return resolve_engine(c, kp, c->n_real > 0 ? c->n_real : 1, &plan);
+    return resolve_engine(c, kp, c->n_real > 0 ? c->n_real : 1, &plan, nullptr);
 }
 
 llg_status llg_get_coefficients(const llg_ctx *c, double out[LLG_NCOEFF])

@@ -662,8 +662,9 @@ bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_ki
     if (bytes > (size_t)smem_optin) return false;
     int R = force_rows;
     if (R == 0) {
-        // fewest rows per thread that fit; three rows per thread for the b = 1 rod (1344 rows)
-        R = rows <= 768 ? 1 : (rows <= 1536 ? 3 : 4);
+        // fewest rows per thread that fit (two rows per thread for the b = 1 rod's 1344 rows:
+        // 672 threads measured ahead of 448 x 3 rows on GB300)
+        R = rows <= 768 ? 1 : (rows <= 1344 ? 2 : (rows <= 1536 ? 3 : 4));
     }
     if (R < 1 || R > 4 || (rows + R - 1) / R > pipelined_max_threads(R)) return false;
     plan->kind = 2;

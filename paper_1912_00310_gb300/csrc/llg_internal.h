@@ -95,6 +95,18 @@ cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_r
                         long long step0, long long n_steps, float *samples, int *status,
                         unsigned *flags, cudaStream_t st);
 
+// ---- streaming engine (k_slab.cu): one fused Heun step per launch over HBM ----------------
+struct SlabPlan {
+    int tiles_x, tiles_y, TXmax, TYmax, cols_per_thread, threads;
+    size_t smem_bytes;
+};
+bool slab_plan(const KParams &p, int dev, SlabPlan *plan);
+// buf_a, buf_b: n_real * ncells float4 each; partial: slab_partial_floats(n_real) floats.
+cudaError_t slab_advance(const KParams &p, const SlabPlan &plan, float *m, int n_real, long long step0,
+                         long long n_steps, float *samples, int *status, float4 *buf_a, float4 *buf_b,
+                         float *partial, cudaStream_t st, long long *launches);
+size_t slab_partial_floats(int n_real);
+
 // ---- host runtime helpers (api.cpp) ---------------------------------------------------------
 // Store a message for llg_last_error() on this thread.
 void set_last_error(const char *msg);
