@@ -112,7 +112,7 @@ class Clocks:
 
 def make_grid(pkg, cfg, engine):
     from workloads import MAGNETITE as M
-    g = pkg.Grid(*cfg["dims"], a0=M["a0"], b=cfg["b"])
+    g = pkg.Grid(*cfg["dims"], a0=M["a0"], b=cfg["b"], periodic=cfg.get("periodic", 0))
     g.set_material(A0=M["A0"], Ms=M["Ms"], K0=M["K0"], alpha=M["alpha"], T=M["T"])
     g.set_scaling(mode=cfg["mode"], Tc=M["Tc"])
     g.set_sweep(H_start=cfg["H_start"], H_turn=cfg["H_turn"], rate=cfg["rate"], dt=cfg["dt"],
@@ -373,6 +373,10 @@ def profile_case(name):
     elif name == "b4":
         cfg = dict(CONFIGS["rod_b4_4real"])
         n_real, steps, eng = 608, 2000, pkg.ENGINE_RESIDENT
+    elif name == "slab":
+        # the 512x512x56 periodic slab (14.7M cells, 470 MB of state buffers), a few Heun steps
+        cfg = dict(CONFIGS["slab_512x512x56"], sample_dH=1.0)
+        n_real, steps, eng = 1, 4, pkg.ENGINE_STREAM
     else:
         raise SystemExit(f"unknown profile case {name}")
     g = make_grid(pkg, cfg, eng)

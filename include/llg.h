@@ -182,6 +182,26 @@ llg_status llg_set_state(llg_ctx *ctx, const float *m, int64_t step);
  * LLG_ETIMEOUT.  Errors from earlier asynchronous work surface here as ECUDA. */
 llg_status llg_sync(llg_ctx *ctx, double timeout_s);
 
+/* Uneven batch (the realisation ensembles of the loop paragraph, for several b, sweep rates and
+ * damping values at once): advance every job -- a context with an ensemble from llg_reset --
+ * by min(max_steps, the steps left in its loop) Heun steps with the resident engine, all jobs in
+ * one launch: a CUDA graph with one kernel node per job on independent branches, ordered
+ * longest first, launched on jobs[0]'s stream after the work queued on every job's stream.
+ * m_samples (optional) [n_jobs] device sample arrays, one per job, as for llg_advance.
+ * steps_done (optional, host) [n_jobs] receives the steps each job advanced.  Asynchronous.
+ * Errors: EINVAL (no ensemble, jobs on different devices), EUNSUPPORTED (a grid the resident
+ * engine cannot hold), ECUDA. */
+llg_status llg_run_batch(llg_ctx *const *jobs, int n_jobs, int64_t max_steps,
+                         float *const *m_samples, int64_t *steps_done);
+
+/* Choose the resident engine's launch shape for this context by timing the candidates (rows per
+ * thread of the plane-pipelined kernel; rods per CTA of the two-phase kernel) for trial_steps
+ * Heun steps each on a scratch copy of the ensemble (allocated and freed here), and set them
+ * with llg_set_tuning.  Results are cached per (device, grid, realisation count) for the life of
+ * the process.  The ensemble itself is not advanced.  best_rate (optional) receives the fastest
+ * cell-steps/s.  Synchronises.  Errors: EINVAL (no ensemble), ENOMEM, EUNSUPPORTED. */
+llg_status llg_autotune(llg_ctx *ctx, int64_t trial_steps, double *best_rate);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Queries and host-side loop analysis                                                       */
 /* ---------------------------------------------------------------------------------------- */

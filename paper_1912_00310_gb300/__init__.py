@@ -15,7 +15,7 @@ from ._lib import (COEFF_NAMES, ENGINE_AUTO, ENGINE_PLAIN, ENGINE_RESIDENT, ENGI
                    TUNE_ROWS_PER_THREAD, LLGError,
                    LoopStats)
 
-__all__ = ["Grid", "LLGError", "LoopStats", "loop_stats", "ENGINE_AUTO", "ENGINE_RESIDENT",
+__all__ = ["Grid", "run_batch", "LLGError", "LoopStats", "loop_stats", "ENGINE_AUTO", "ENGINE_RESIDENT",
            "ENGINE_PLAIN", "ENGINE_STREAM", "TUNE_ROD_KIND", "TUNE_RODS_PER_CTA", "TUNE_CHUNK_STEPS",
            "TUNE_ROWS_PER_THREAD", "TUNE_GENERIC_KERNEL", "TUNE_BALANCE",
            "library"]
@@ -162,6 +162,25 @@ class Grid:
 
     def sync(self, timeout_s: float = 0.0):
         _lib.check(self._L.llg_sync(self._h, timeout_s))
+
+    def autotune(self, trial_steps: int = 200) -> float:
+        rate = C.c_double()
+        _lib.check(self._L.llg_autotune(self._h, int(trial_steps), C.byref(rate)))
+        return rate.value
+
+
+def run_batch(grids, max_steps: int, samples=None):
+    """Advance every grid's ensemble by min(max_steps, steps left in its loop) in one launch
+    (a CUDA graph with one node per grid); returns the steps each grid advanced."""
+    L = _lib.load()
+    n = len(grids)
+    hs = (C.c_void_p * n)(*[g._h.value for g in grids])
+    sp = None
+    if samples is not None:
+        sp = (C.c_void_p * n)(*[_ptr(s) if s is not None else None for s in samples])
+    done = (C.c_int64 * n)()
+    _lib.check(L.llg_run_batch(hs, n, int(max_steps), sp, done))
+    return list(done)
 
 
 def loop_stats(samples: np.ndarray, H: np.ndarray, k_turn: int, mode=1, zeta=1.0, delta=0.511):

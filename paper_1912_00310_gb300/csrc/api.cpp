@@ -144,6 +144,40 @@ int resolve_engine(const llg_ctx *c, const llg::KParams &kp, int n_real, llg::Ro
 namespace llg {
 void set_last_error(const char *msg) { std::snprintf(g_err, sizeof g_err, "%s", msg); }
 
+llg_status ctx_view(llg_ctx *c, CtxView *v)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    Derived d;
+    const llg_status s = derived_of(c, &d);
+    if (s != LLG_OK) return s;
+    if (c->n_real > 0 && c->flags_cap < (size_t)c->n_real) {
+        DeviceGuard g(c->device);
+        cudaFree(c->d_flags);
+        c->d_flags = nullptr;
+        c->flags_cap = 0;
+        LLG_CUDA(cudaMalloc(&c->d_flags, sizeof(unsigned) * (size_t)c->n_real), "cudaMalloc(flags)");
+        c->flags_cap = (size_t)c->n_real;
+    }
+    v->device = c->device;
+    v->stream = c->stream;
+    v->n_real = c->n_real;
+    v->d_m = c->d_m;
+    v->d_status = c->d_status;
+    v->d_flags = c->d_flags;
+    v->step = c->step;
+    v->steps_per_loop = d.steps_per_loop;
+    v->kp = kparams_of(d, c->nx, c->ny, c->nz, c->periodic, c->sw.dt);
+    v->kp.seed = c->seed;
+    v->kp.real0 = c->real0;
+    v->tune_kind = c->tune_kind;
+    v->tune_rods = c->tune_rods;
+    v->tune_rows = c->tune_rows;
+    v->tune_generic = c->tune_generic != 0;
+    return LLG_OK;
+}
+
+void ctx_add_steps(llg_ctx *c, long long n) { c->step += n; }
+
 llg_status kparams_from_ctx(const llg_ctx *c, KParams *out)
 {
     Derived d;

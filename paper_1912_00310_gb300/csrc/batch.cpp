@@ -1,0 +1,246 @@
+// batch.cpp -- the batching layer and the autotuner of the resident engine.
+//
+// llg_run_batch: uneven jobs (rods of different size b, sweep rates and damping, each job a
+// context with its own ensemble) advance together in ONE launch: a CUDA graph with one kernel
+// node per job on independent branches, so the hardware runs the jobs' CTAs side by side and the
+// small-rod CTAs fill the wave tails of the large ones.  Jobs are ordered longest first (the
+// block scheduler starts branches roughly in capture order).  The graph is captured and
+// instantiated per call (a few hundred microseconds against launches of tens of milliseconds).
+//
+// llg_autotune: times the resident engine's launch shapes (rows per thread of the
+// plane-pipelined kernel, rods per CTA of the two-phase kernel) on a scratch copy of a context's
+// ensemble and keeps the fastest, cached per (device, grid, realisation count).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/llg.h"
+#include "llg_internal.h"
+
+namespace {
+
+struct TuneKey {
+    std::string device;
+    int nx, ny, nz, n_real;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(device, nx, ny, nz, n_real) < std::tie(o.device, o.nx, o.ny, o.nz, o.n_real);
+    }
+};
+struct TuneValue {
+    int kind, rods, rows;
+    double rate;
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneValue> g_tune_cache;
+
+}  // namespace
+
+extern "C" llg_status llg_autotune(llg_ctx *ctx, int64_t trial_steps, double *best_rate)
+{
+    if (!ctx || trial_steps < 1) {
+        llg::set_last_error("need a context and trial_steps >= 1");
+        return LLG_EINVAL;
+    }
+    llg::CtxView v;
+    llg_status s = llg::ctx_view(ctx, &v);
+    if (s != LLG_OK) return s;
+    if (v.n_real < 1 || !v.d_m) {
+        llg::set_last_error("autotune needs an ensemble (llg_reset first)");
+        return LLG_EINVAL;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, v.device) != cudaSuccess) {
+        llg::set_last_error("cudaGetDeviceProperties failed");
+        return LLG_ECUDA;
+    }
+    const TuneKey key{prop.name, v.kp.nx, v.kp.ny, v.kp.nz, v.n_real};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            llg_set_tuning(ctx, LLG_TUNE_ROD_KIND, it->second.kind);
+            llg_set_tuning(ctx, LLG_TUNE_RODS_PER_CTA, it->second.rods);
+            llg_set_tuning(ctx, LLG_TUNE_ROWS_PER_THREAD, it->second.rows);
+            if (best_rate) *best_rate = it->second.rate;
+            return LLG_OK;
+        }
+    }
+    // candidates: (kind, rods per CTA, rows per thread); 0 = automatic
+    std::vector<std::tuple<int, int, int>> cand;
+    for (int rows : {0, 1, 2, 3, 4}) cand.emplace_back(2, 0, rows);
+    for (int rods : {0, 1, 2, 4, 8, 16, 32}) cand.emplace_back(1, rods, 0);
+    const size_t bytes = (size_t)v.n_real * (size_t)v.kp.ncells * 3 * sizeof(float);
+    float *scratch = nullptr;
+    if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        llg::set_last_error("autotune scratch allocation failed");
+        return LLG_ENOMEM;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = -1.0;
+    TuneValue bestv{0, 0, 0, 0.0};
+    for (auto [kind, rods, rows] : cand) {
+        llg::RodPlan plan{};
+        if (!llg::rod_plan(v.kp, v.n_real, v.device, &plan, kind, rods, rows)) continue;
+        if (kind == 2 && rows == 0 && plan.kind != 2) continue;
+        plan.balance = true;
+        double t_best = 1e30;
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) {
+            cudaMemcpyAsync(scratch, v.d_m, bytes, cudaMemcpyDeviceToDevice, v.stream);
+            cudaEventRecord(e0, v.stream);
+            ok = llg::rod_advance(v.kp, plan, scratch, v.n_real, v.step, trial_steps, nullptr, v.d_status,
+                                  v.d_flags, v.stream) == cudaSuccess;
+            cudaEventRecord(e1, v.stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t_best = std::min(t_best, (double)ms);
+        }
+        cudaGetLastError();
+        if (!ok) continue;
+        const double rate = (double)v.n_real * v.kp.ncells * trial_steps / (t_best * 1e-3);
+        if (rate > best) {
+            best = rate;
+            bestv = TuneValue{kind, rods, rows, rate};
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scratch);
+    if (best <= 0.0) {
+        llg::set_last_error("no resident launch shape can hold this grid");
+        return LLG_EUNSUPPORTED;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = bestv;
+    }
+    llg_set_tuning(ctx, LLG_TUNE_ROD_KIND, bestv.kind);
+    llg_set_tuning(ctx, LLG_TUNE_RODS_PER_CTA, bestv.rods);
+    llg_set_tuning(ctx, LLG_TUNE_ROWS_PER_THREAD, bestv.rows);
+    if (best_rate) *best_rate = best;
+    return LLG_OK;
+}
+
+extern "C" llg_status llg_run_batch(llg_ctx *const *jobs, int n_jobs, int64_t max_steps,
+                                    float *const *m_samples, int64_t *steps_done)
+{
+    if (!jobs || n_jobs < 1 || max_steps < 0) {
+        llg::set_last_error("need jobs, n_jobs >= 1, max_steps >= 0");
+        return LLG_EINVAL;
+    }
+    std::vector<llg::CtxView> views((size_t)n_jobs);
+    std::vector<long long> steps((size_t)n_jobs);
+    std::vector<llg::RodPlan> plans((size_t)n_jobs);
+    for (int j = 0; j < n_jobs; ++j) {
+        llg_status s = llg::ctx_view(jobs[j], &views[(size_t)j]);
+        if (s != LLG_OK) return s;
+        const llg::CtxView &v = views[(size_t)j];
+        if (v.n_real < 1 || !v.d_m) {
+            llg::set_last_error("every batch job needs an ensemble (llg_reset first)");
+            return LLG_EINVAL;
+        }
+        if (v.device != views[0].device) {
+            llg::set_last_error("all batch jobs must be on one device");
+            return LLG_EINVAL;
+        }
+        // steps left in the job's loop (a constant field runs max_steps)
+        const long long left = v.steps_per_loop > 0 ? std::max(0LL, v.steps_per_loop - v.step) : max_steps;
+        steps[(size_t)j] = std::min<long long>(left, max_steps);
+        if (!llg::rod_plan(v.kp, v.n_real, v.device, &plans[(size_t)j], v.tune_kind, v.tune_rods, v.tune_rows)) {
+            char msg[128];
+            std::snprintf(msg, sizeof msg, "batch job %d: the resident engine cannot hold its grid", j);
+            llg::set_last_error(msg);
+            return LLG_EUNSUPPORTED;
+        }
+        plans[(size_t)j].balance = false;  // jobs share the GPU; no co-resident grid per job
+        plans[(size_t)j].generic = v.tune_generic;
+    }
+    // longest first: cell-steps of the job
+    std::vector<int> order((size_t)n_jobs);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const double wa = (double)views[(size_t)a].n_real * views[(size_t)a].kp.ncells * steps[(size_t)a];
+        const double wb = (double)views[(size_t)b].n_real * views[(size_t)b].kp.ncells * steps[(size_t)b];
+        return wa > wb;
+    });
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(views[0].device);
+    const cudaStream_t origin = views[0].stream;
+    cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> br((size_t)n_jobs, nullptr);
+    std::vector<cudaEvent_t> ev((size_t)n_jobs + 1, nullptr);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    llg_status status = LLG_OK;
+    auto check = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && status == LLG_OK) {
+            char msg[256];
+            std::snprintf(msg, sizeof msg, "batch %s: %s", what, cudaGetErrorString(e));
+            llg::set_last_error(msg);
+            status = LLG_ECUDA;
+        }
+        return e == cudaSuccess;
+    };
+    check(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "stream");
+    for (int j = 0; j < n_jobs && status == LLG_OK; ++j) check(cudaStreamCreateWithFlags(&br[(size_t)j], cudaStreamNonBlocking), "stream");
+    for (auto &e : ev)
+        if (status == LLG_OK) check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    if (status == LLG_OK && check(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "capture")) {
+        check(cudaEventRecord(ev[0], cap), "record");
+        for (int j : order) {
+            const llg::CtxView &v = views[(size_t)j];
+            cudaStream_t s = br[(size_t)j];
+            check(cudaStreamWaitEvent(s, ev[0], 0), "fork");
+            if (steps[(size_t)j] > 0)
+                check(llg::rod_advance(v.kp, plans[(size_t)j], v.d_m, v.n_real, v.step, steps[(size_t)j],
+                                       m_samples ? m_samples[j] : nullptr, v.d_status, v.d_flags, s),
+                      "launch");
+            check(cudaEventRecord(ev[(size_t)j + 1], s), "record");
+            check(cudaStreamWaitEvent(cap, ev[(size_t)j + 1], 0), "join");
+        }
+        const cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        check(e, "end capture");
+    }
+    if (status == LLG_OK && check(cudaGraphInstantiate(&exec, graph, 0), "instantiate")) {
+        // the graph runs after the work already queued on the jobs' streams
+        for (int j = 0; j < n_jobs && status == LLG_OK; ++j) {
+            check(cudaEventRecord(ev[(size_t)j + 1], views[(size_t)j].stream), "order");
+            check(cudaStreamWaitEvent(origin, ev[(size_t)j + 1], 0), "order");
+        }
+        if (status == LLG_OK) check(cudaGraphLaunch(exec, origin), "graph launch");
+        if (status == LLG_OK) {
+            check(cudaEventRecord(ev[0], origin), "order");
+            for (int j = 0; j < n_jobs && status == LLG_OK; ++j)
+                check(cudaStreamWaitEvent(views[(size_t)j].stream, ev[0], 0), "order");
+        }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto e : ev)
+        if (e) cudaEventDestroy(e);
+    for (auto s : br)
+        if (s) cudaStreamDestroy(s);
+    if (cap) cudaStreamDestroy(cap);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (status != LLG_OK) return status;
+    for (int j = 0; j < n_jobs; ++j) {
+        llg::ctx_add_steps(jobs[j], steps[(size_t)j]);
+        if (steps_done) steps_done[j] = steps[(size_t)j];
+    }
+    return LLG_OK;
+}

@@ -116,4 +116,21 @@ namespace llg {
 // Kernel parameters of a context's grid, material, scaling and sweep (host-side derivation
 // only; seed and real0 are left zero).  Returns LLG_OK or the setup error (message stored).
 llg_status kparams_from_ctx(const llg_ctx *ctx, KParams *out);
+
+// A context's ensemble and launch settings, for the batching layer and the autotuner.  Makes
+// sure the hand-off flags of the resident engine exist when there is an ensemble.
+struct CtxView {
+    int device;
+    cudaStream_t stream;
+    int n_real;
+    float *d_m;
+    int *d_status;
+    unsigned *d_flags;
+    long long step, steps_per_loop;
+    KParams kp;  // with the ensemble's seed and real0
+    int tune_kind, tune_rods, tune_rows;
+    bool tune_generic;
+};
+llg_status ctx_view(llg_ctx *ctx, CtxView *out);
+void ctx_add_steps(llg_ctx *ctx, long long n);
 }  // namespace llg
