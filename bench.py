@@ -349,12 +349,109 @@ def side_measurements(args, torch, pkg, cfg, g, samples, S_per_step, flush):
         g1.close()
     out["plain_same_workload"] = {"value": plain_rate, "unit": UNIT,
                                   "resident_over_plain": None}
+    out["ladder_batch"] = ladder_batch(args, torch, pkg, flush)
+    out["slab_512x512x56"] = slab_stream(args, torch, pkg, flush)
     out["small_rod_b4_4real"] = {
         "resident_cell_steps_per_s": res["resident"], "plain_cell_steps_per_s": res["plain"],
         "resident_over_plain": res["resident"] / res["plain"],
         "resident_loops_per_s": res["resident"] / (ncell1 * spl),
         "plain_loops_per_s": res["plain"] / (ncell1 * spl)}
     return out
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s if the driver wrote it, else the
+    recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = json.load(f).get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    except (OSError, ValueError):
+        pass
+    return 6800.0, "fallback"
+
+
+def ladder_batch(args, torch, pkg, flush):
+    """The uneven ladder: b in {1,2,4,8} x rate in {1000,100,10} Oe/ns x alpha in
+    {0.05,0.1,0.5,1.0}, 64 realisations each (3072 loops), advanced W Heun steps per call in one
+    graph launch, against the same jobs run one after another with the plain engine."""
+    from workloads import CONFIGS, DT_BY_B, MAGNETITE as M, ROD_DIMS
+    c3 = CONFIGS["ladder_batch"]
+    jobs, specs = [], []
+    for b in c3["bs"]:
+        for rate in c3["rates"]:
+            for alpha in c3["alphas"]:
+                g = pkg.Grid(*ROD_DIMS[b], a0=M["a0"], b=b)
+                g.set_material(A0=M["A0"], Ms=M["Ms"], K0=M["K0"], alpha=alpha, T=M["T"])
+                g.set_scaling(mode=c3["mode"], Tc=M["Tc"])
+                g.set_sweep(H_start=c3["H_start"], H_turn=c3["H_turn"], rate=rate, dt=DT_BY_B[b],
+                            sample_dH=c3["sample_dH"])
+                g.set_engine(pkg.ENGINE_RESIDENT)
+                g.reset(seed=c3["seed"], n_real=c3["n_real"], real_offset=len(jobs) * c3["n_real"])
+                jobs.append(g)
+                specs.append((b, rate, alpha))
+    tuned = {}
+    for g, (b, _, _) in zip(jobs, specs):
+        if b not in tuned:
+            tuned[b] = g.autotune(trial_steps=100)
+        else:
+            g.autotune(trial_steps=100)  # cached: same shape
+    samples = [torch.zeros((c3["n_real"], g.n_samples), device="cuda") for g in jobs]
+    W = 1000
+    cells = sum(c3["n_real"] * g.ncells for g in jobs)
+    ts = timed_steps(torch, lambda: pkg.run_batch(jobs, W, samples), args.steps, 1, flush)
+    rate = cells * W * args.steps / sum(ts)
+    loops_per_s = sum(c3["n_real"] * W / g.steps_per_loop for g in jobs) * args.steps / sum(ts)
+    # the same jobs, one after another, with the plain engine (a short window each)
+    Wp = 20
+    t_plain = 0.0
+    for g in jobs:
+        g.set_engine(pkg.ENGINE_PLAIN)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for g, S in zip(jobs, samples):
+        g.advance(2, S)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for g, S in zip(jobs, samples):
+        g.advance(Wp, S)
+    e1.record(st)
+    e1.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3
+    plain_rate = cells * Wp / t_plain
+    for g in jobs:
+        g.close()
+    return {"jobs": len(jobs), "loops": len(jobs) * c3["n_real"], "heun_steps_per_call": W,
+            "cell_steps_per_call": cells * W, "value": rate, "unit": UNIT,
+            "loops_per_s": loops_per_s, "plain_sequential_cell_steps_per_s": plain_rate,
+            "batched_over_plain": rate / plain_rate,
+            "autotuned_cell_steps_per_s_by_b": {str(k): v for k, v in tuned.items()},
+            "launch": "one CUDA graph per call (one kernel node per job, longest first)"}
+
+
+def slab_stream(args, torch, pkg, flush):
+    """The 512x512x56 periodic slab with the streaming engine: one fused Heun step per launch."""
+    from workloads import CONFIGS
+    c4 = dict(CONFIGS["slab_512x512x56"], sample_dH=1.0)
+    g = make_grid(pkg, c4, pkg.ENGINE_STREAM)
+    g.reset(seed=c4["seed"], n_real=1)
+    S = torch.zeros((1, g.n_samples), device="cuda")
+    W = 100
+    ts = timed_steps(torch, lambda: g.advance(W, S), args.steps, 1, flush)
+    t_step = sum(ts) / (W * args.steps)
+    rate = g.ncells / t_step
+    peak, basis = hbm_peak_gbs()
+    alg = 24.0 * rate / 1e9   # 12 B in + 12 B out per cell-step
+    phys = 32.0 * rate / 1e9  # float4 state in and out
+    ncells = g.ncells
+    g.close()
+    return {"cells": ncells, "value": rate, "unit": UNIT, "ms_per_heun_step": 1e3 * t_step,
+            "hbm_algorithmic_gbs": alg, "hbm_float4_gbs": phys, "hbm_peak_gbs": peak,
+            "hbm_peak_basis": basis, "hbm_frac_algorithmic": alg / peak,
+            "alu_frac": ALU_OPS_PER_CELL_STEP * rate / (152 * ALU_LANES_PER_SM * MAX_SM_MHZ * 1e6),
+            "l2": "state (470 MB ping-pong) larger than L2"}
 
 
 def profile_case(name):

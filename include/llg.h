@@ -202,6 +202,27 @@ llg_status llg_run_batch(llg_ctx *const *jobs, int n_jobs, int64_t max_steps,
  * cell-steps/s.  Synchronises.  Errors: EINVAL (no ensemble), ENOMEM, EUNSUPPORTED. */
 llg_status llg_autotune(llg_ctx *ctx, int64_t trial_steps, double *best_rate);
 
+/* Pathwise gradient of a loop loss with respect to the calibration scale factors
+ * (s_K, s_alpha, s_Ms) of llg_set_scaling (the coarse-grained parameters of Eqs. 8-9 are fitted
+ * to a finer loop), with the thermal normals of every (realisation, cell, step) held fixed.
+ * The window is the n_steps Heun steps from the ensemble's current step; the ensemble is not
+ * advanced.  Samples of the window: the realisation means mbar_k of the cell-averaged m_z after
+ * the steps k * sample_every in (step, step + n_steps].
+ *   objective 0: L = (1/K) sum_k (mbar_k - target[k])^2, target host array indexed by the global
+ *                sample number (length llg_num_samples)
+ *   objective 1: L = sum_k (mbar_k + mbar_k+1)/2 (H_k+1 - H_k), the signed area under the
+ *                window's mean loop (target unused)
+ * Method: a forward pass with the resident engine storing the state every ckpt_every steps,
+ * then, segment by segment from the last, a kernel that recomputes the segment's states from its
+ * checkpoint and runs the reverse-mode adjoint of the Heun step back through them (one CTA per
+ * realisation; rods of at most 1024 cells with free faces).  Allocates its scratch (states of
+ * one segment and the checkpoints) for the duration of the call; synchronises.
+ * loss_out (optional) receives L; grad_out receives dL/d(s_K, s_alpha, s_Ms).
+ * Errors: EINVAL (no ensemble, no sample in the window, window past the loop end),
+ * EUNSUPPORTED (grid), ENOMEM, ECUDA. */
+llg_status llg_loop_area_grad(llg_ctx *ctx, int64_t n_steps, int objective, const double *target,
+                              int64_t ckpt_every, double *loss_out, double grad_out[3]);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Queries and host-side loop analysis                                                       */
 /* ---------------------------------------------------------------------------------------- */

@@ -503,3 +503,276 @@ double orc_specific_loss_power(double f_hz, double Ms, double S_Oe, double rho_g
     double w_per_m3 = f_hz * ORC_MU0 * ORC_OE_TO_AM * Ms * S_Oe;
     return w_per_m3 / (rho_g_cm3 * 1.0e6);
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Gradient of a loop-mismatch loss with respect to the calibration scale factors              */
+/* (s_K, s_alpha, s_Ms), by forward-mode differentiation of the discrete Heun map.             */
+/*                                                                                             */
+/* The scale factors multiply K(b), alpha (everywhere it appears: g1, alpha g1 and the thermal */
+/* variance) and Ms (in the exchange and anisotropy fields and the thermal variance; m stays a */
+/* unit vector).  The thermal normals of each (realisation, cell, step) are fixed (pathwise,   */
+/* common random numbers).  Every quantity carries its value and its derivatives along the    */
+/* three scale factors; the arithmetic is the same as heun_step's.                             */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+    double v, d[3];
+} dual;
+
+static dual dconst(double v)
+{
+    dual r = {v, {0.0, 0.0, 0.0}};
+    return r;
+}
+static dual dadd(dual a, dual b)
+{
+    dual r = {a.v + b.v, {a.d[0] + b.d[0], a.d[1] + b.d[1], a.d[2] + b.d[2]}};
+    return r;
+}
+static dual dsub(dual a, dual b)
+{
+    dual r = {a.v - b.v, {a.d[0] - b.d[0], a.d[1] - b.d[1], a.d[2] - b.d[2]}};
+    return r;
+}
+static dual dmul(dual a, dual b)
+{
+    dual r;
+    r.v = a.v * b.v;
+    for (int k = 0; k < 3; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+}
+static dual ddiv(dual a, dual b)
+{
+    dual r;
+    r.v = a.v / b.v;
+    for (int k = 0; k < 3; ++k) r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v);
+    return r;
+}
+static dual dsqrt(dual a)
+{
+    dual r;
+    r.v = sqrt(a.v);
+    for (int k = 0; k < 3; ++k) r.d[k] = a.d[k] / (2.0 * r.v);
+    return r;
+}
+static dual dscale(double s, dual a)
+{
+    dual r = {s * a.v, {s * a.d[0], s * a.d[1], s * a.d[2]}};
+    return r;
+}
+
+typedef struct {
+    dual x, y, z;
+} dvec;
+
+static dvec dv_add(dvec a, dvec b)
+{
+    dvec r = {dadd(a.x, b.x), dadd(a.y, b.y), dadd(a.z, b.z)};
+    return r;
+}
+static dvec dv_scale(dual s, dvec a)
+{
+    dvec r = {dmul(s, a.x), dmul(s, a.y), dmul(s, a.z)};
+    return r;
+}
+static dvec dv_cross(dvec a, dvec b)
+{
+    dvec r = {dsub(dmul(a.y, b.z), dmul(a.z, b.y)), dsub(dmul(a.z, b.x), dmul(a.x, b.z)),
+              dsub(dmul(a.x, b.y), dmul(a.y, b.x))};
+    return r;
+}
+static dvec dv_normalise(dvec a)
+{
+    dual n = dsqrt(dadd(dadd(dmul(a.x, a.x), dmul(a.y, a.y)), dmul(a.z, a.z)));
+    dvec r = {ddiv(a.x, n), ddiv(a.y, n), ddiv(a.z, n)};
+    return r;
+}
+
+typedef struct {
+    dual c_ex, c_an, g1, ag1, sigma;
+} dcoeffs;
+
+/* Coefficients of Eq. 1 and of the thermal field as functions of the three scale factors. */
+static dcoeffs dual_coefficients(const orc_problem *p, const double scale[3])
+{
+    dual sK = {scale[0], {1.0, 0.0, 0.0}};
+    dual sA = {scale[1], {0.0, 1.0, 0.0}};
+    dual sM = {scale[2], {0.0, 0.0, 1.0}};
+    dual K = dscale(p->K, sK), alpha = dscale(p->alpha, sA), Ms = dscale(p->Ms, sM);
+    const double g0 = ORC_MU0 * ORC_GE;
+    dcoeffs c;
+    c.c_ex = ddiv(dconst(2.0 * p->A / (ORC_MU0 * p->a * p->a)), Ms);
+    c.c_an = ddiv(dscale(2.0 / ORC_MU0, K), Ms);
+    c.g1 = ddiv(dconst(g0), dadd(dconst(1.0), dmul(alpha, alpha)));
+    c.ag1 = dmul(alpha, c.g1);
+    c.sigma = p->T > 0.0 ? dsqrt(ddiv(dscale(2.0 * ORC_KB * p->T / (g0 * ORC_MU0 * p->volume * p->dt), alpha), Ms))
+                         : dconst(0.0);
+    return c;
+}
+
+static dvec dual_field(const orc_problem *p, const dcoeffs *c, const dvec *m, int x, int y, int z,
+                       double Hz, dvec hth)
+{
+    dvec s = {dconst(0.0), dconst(0.0), dconst(0.0)};
+    const int dims[3] = {p->nx, p->ny, p->nz};
+    const int pos[3] = {x, y, z};
+    for (int axis = 0; axis < 3; ++axis) {
+        for (int dir = -1; dir <= 1; dir += 2) {
+            int q[3] = {pos[0], pos[1], pos[2]};
+            q[axis] += dir;
+            if (q[axis] < 0 || q[axis] >= dims[axis]) {
+                if (!(p->periodic & (1u << axis))) continue;
+                q[axis] = (q[axis] + dims[axis]) % dims[axis];
+            }
+            int64_t j = q[0] + (int64_t)p->nx * (q[1] + (int64_t)p->ny * q[2]);
+            s = dv_add(s, m[j]);
+        }
+    }
+    int64_t i = x + (int64_t)p->nx * (y + (int64_t)p->ny * z);
+    /* easy axis along z: anisotropy field c_an m_z z */
+    dvec H = dv_add(dv_scale(c->c_ex, s), hth);
+    H.z = dadd(H.z, dadd(dmul(c->c_an, m[i].z), dconst(Hz)));
+    return H;
+}
+
+static dvec dual_rhs(const dcoeffs *c, dvec m, dvec H)
+{
+    dvec mxH = dv_cross(m, H);
+    dvec mxmxH = dv_cross(m, mxH);
+    dvec r = dv_add(dv_scale(dscale(-1.0, c->g1), mxH), dv_scale(dscale(-1.0, c->ag1), mxmxH));
+    return r;
+}
+
+typedef struct {
+    const orc_problem *p;
+    const double *scale;
+    uint32_t seed, real0;
+    int n_real;
+    int64_t step0, n_steps, sample_every;
+    const double *m0;      /* [n_real][N][3] */
+    dual *mean_samples;    /* [n_samples_window], sums over realisations (each thread adds) */
+    int64_t k_first, n_k;  /* sample numbers in the window */
+    int next_real;
+    pthread_mutex_t lock;
+} grad_job;
+
+static void *grad_worker(void *arg)
+{
+    grad_job *J = (grad_job *)arg;
+    const orc_problem *p = J->p;
+    const int64_t N = ncells_of(p);
+    const dcoeffs c = dual_coefficients(p, J->scale);
+    const double dt = p->dt;
+    dvec *m = (dvec *)malloc(sizeof(dvec) * (size_t)N);
+    dvec *mt = (dvec *)malloc(sizeof(dvec) * (size_t)N);
+    dvec *f0 = (dvec *)malloc(sizeof(dvec) * (size_t)N);
+    dvec *hth = (dvec *)malloc(sizeof(dvec) * (size_t)N);
+    dual *local = (dual *)calloc((size_t)J->n_k, sizeof(dual));
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int r = J->next_real++;
+        pthread_mutex_unlock(&J->lock);
+        if (r >= J->n_real) break;
+        for (int64_t i = 0; i < N; ++i) {
+            const double *mi = J->m0 + ((int64_t)r * N + i) * 3;
+            m[i].x = dconst(mi[0]);
+            m[i].y = dconst(mi[1]);
+            m[i].z = dconst(mi[2]);
+        }
+        for (int64_t s = 0; s < J->n_steps; ++s) {
+            const int64_t n = J->step0 + s;
+            const double Hn = orc_field_Oe(p, n) * ORC_OE_TO_AM, Hn1 = orc_field_Oe(p, n + 1) * ORC_OE_TO_AM;
+            for (int64_t i = 0; i < N; ++i) {
+                double xi[3];
+                orc_thermal_normals(J->seed, J->real0 + (uint32_t)r, (uint32_t)i, (uint64_t)n, xi);
+                hth[i].x = dscale(xi[0], c.sigma);
+                hth[i].y = dscale(xi[1], c.sigma);
+                hth[i].z = dscale(xi[2], c.sigma);
+            }
+            for (int z = 0; z < p->nz; ++z)
+                for (int y = 0; y < p->ny; ++y)
+                    for (int x = 0; x < p->nx; ++x) {
+                        int64_t i = x + (int64_t)p->nx * (y + (int64_t)p->ny * z);
+                        dvec H = dual_field(p, &c, m, x, y, z, Hn, hth[i]);
+                        f0[i] = dual_rhs(&c, m[i], H);
+                        mt[i] = dv_normalise(dv_add(m[i], dv_scale(dconst(dt), f0[i])));
+                    }
+            for (int z = 0; z < p->nz; ++z)
+                for (int y = 0; y < p->ny; ++y)
+                    for (int x = 0; x < p->nx; ++x) {
+                        int64_t i = x + (int64_t)p->nx * (y + (int64_t)p->ny * z);
+                        dvec H = dual_field(p, &c, mt, x, y, z, Hn1, hth[i]);
+                        dvec f1 = dual_rhs(&c, mt[i], H);
+                        m[i] = dv_normalise(dv_add(m[i], dv_scale(dconst(0.5 * dt), dv_add(f0[i], f1))));
+                    }
+            const int64_t done = n + 1;
+            if (J->sample_every > 0 && done % J->sample_every == 0) {
+                const int64_t k = done / J->sample_every - J->k_first;
+                if (k >= 0 && k < J->n_k) {
+                    dual acc = dconst(0.0);
+                    for (int64_t i = 0; i < N; ++i) acc = dadd(acc, m[i].z);
+                    local[k] = dadd(local[k], dscale(1.0 / (double)N, acc));
+                }
+            }
+        }
+    }
+    pthread_mutex_lock(&J->lock);
+    for (int64_t k = 0; k < J->n_k; ++k) J->mean_samples[k] = dadd(J->mean_samples[k], local[k]);
+    pthread_mutex_unlock(&J->lock);
+    free(m);
+    free(mt);
+    free(f0);
+    free(hth);
+    free(local);
+    return NULL;
+}
+
+/* Loss L = (1/K) sum_k (mbar_k - target[k])^2 over the samples k of the window
+ * (step0, step0 + n_steps] (sample k after step k * sample_every), mbar_k the realisation mean of
+ * the cell-averaged m_z, starting from m0 [n_real][N][3] at step0, at the given scale factors.
+ * out[0] = L, out[1..3] = dL/d(s_K, s_alpha, s_Ms); mean_out [K] (optional) = mbar_k.
+ * target is indexed by the global sample number.  Returns the number K of samples used. */
+int64_t orc_loss_grad(const orc_problem *p, const double scale[3], uint32_t seed, int n_real,
+                      uint32_t real0, int64_t step0, int64_t n_steps, const double *m0,
+                      int64_t sample_every, const double *target, double *out, double *mean_out,
+                      int n_threads)
+{
+    const int64_t k_first = step0 / sample_every + 1;
+    const int64_t k_last = (step0 + n_steps) / sample_every;
+    const int64_t n_k = k_last >= k_first ? k_last - k_first + 1 : 0;
+    grad_job J;
+    J.p = p;
+    J.scale = scale;
+    J.seed = seed;
+    J.real0 = real0;
+    J.n_real = n_real;
+    J.step0 = step0;
+    J.n_steps = n_steps;
+    J.sample_every = sample_every;
+    J.m0 = m0;
+    J.mean_samples = (dual *)calloc((size_t)(n_k > 0 ? n_k : 1), sizeof(dual));
+    J.k_first = k_first;
+    J.n_k = n_k;
+    J.next_real = 0;
+    pthread_mutex_init(&J.lock, NULL);
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > n_real) n_threads = n_real;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, grad_worker, &J);
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&J.lock);
+    dual L = dconst(0.0);
+    for (int64_t k = 0; k < n_k; ++k) {
+        dual mbar = dscale(1.0 / (double)n_real, J.mean_samples[k]);
+        if (mean_out) mean_out[k] = mbar.v;
+        dual e = dsub(mbar, dconst(target[k_first + k]));
+        L = dadd(L, dmul(e, e));
+    }
+    if (n_k > 0) L = dscale(1.0 / (double)n_k, L);
+    out[0] = L.v;
+    out[1] = L.d[0];
+    out[2] = L.d[1];
+    out[3] = L.d[2];
+    free(J.mean_samples);
+    return n_k;
+}

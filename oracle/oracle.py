@@ -76,6 +76,9 @@ def lib():
             L.orc_loop_area.argtypes = [dp, dp, C.c_int64]
             L.orc_loop_area.restype = C.c_double
             L.orc_loop_stats.argtypes = [dp, dp, C.c_int, C.c_int64, C.c_int64, dp, dp]
+            L.orc_loss_grad.argtypes = [C.POINTER(_Problem), dp, C.c_uint32, C.c_int, C.c_uint32,
+                                        C.c_int64, C.c_int64, dp, C.c_int64, dp, dp, dp, C.c_int]
+            L.orc_loss_grad.restype = C.c_int64
             L.orc_specific_loss_power.argtypes = [C.c_double] * 4
             L.orc_specific_loss_power.restype = C.c_double
             _lib = L
@@ -275,3 +278,29 @@ def loop_area(H, m) -> float:
 
 def specific_loss_power(f_hz, Ms, S_Oe, rho_g_cm3) -> float:
     return lib().orc_specific_loss_power(f_hz, Ms, S_Oe, rho_g_cm3)
+
+
+def loss_grad(p: Problem, m0: np.ndarray, *, target: np.ndarray, scale=(1.0, 1.0, 1.0), seed=0,
+              real0=0, step0=0, n_steps: int, sample_every: int, threads=None):
+    """Loss L = mean_k (mbar_k - target[k])^2 over the samples of the window and its forward-mode
+    gradient with respect to (s_K, s_alpha, s_Ms) (pathwise: the thermal normals fixed).
+    p is the problem at scale (1, 1, 1); target is indexed by the global sample number.
+    Returns (L, grad[3], mbar[K])."""
+    m0 = np.ascontiguousarray(m0, dtype=np.float64)
+    target = np.ascontiguousarray(target, dtype=np.float64)
+    n_real = m0.shape[0]
+    k_first = step0 // sample_every + 1
+    k_last = (step0 + n_steps) // sample_every
+    out = np.zeros(4)
+    mean = np.zeros(max(1, k_last - k_first + 1))
+    sc = np.ascontiguousarray(scale, dtype=np.float64)
+    pc = p._c()
+    lib().orc_loss_grad(C.byref(pc), _dp(sc), seed & 0xFFFFFFFF, n_real, real0 & 0xFFFFFFFF,
+                        int(step0), int(n_steps), _dp(m0), int(sample_every), _dp(target), _dp(out),
+                        _dp(mean), int(threads or os.cpu_count() or 1))
+    return out[0], out[1:4].copy(), mean[:max(0, k_last - k_first + 1)]
+
+
+def scaled_problem(p: Problem, scale) -> Problem:
+    """The problem with K, alpha and Ms multiplied by (s_K, s_alpha, s_Ms)."""
+    return dataclasses.replace(p, K=p.K * scale[0], alpha=p.alpha * scale[1], Ms=p.Ms * scale[2])

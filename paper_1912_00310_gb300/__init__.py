@@ -15,7 +15,7 @@ from ._lib import (COEFF_NAMES, ENGINE_AUTO, ENGINE_PLAIN, ENGINE_RESIDENT, ENGI
                    TUNE_ROWS_PER_THREAD, LLGError,
                    LoopStats)
 
-__all__ = ["Grid", "run_batch", "LLGError", "LoopStats", "loop_stats", "ENGINE_AUTO", "ENGINE_RESIDENT",
+__all__ = ["Grid", "run_batch", "loop_loss", "LLGError", "LoopStats", "loop_stats", "ENGINE_AUTO", "ENGINE_RESIDENT",
            "ENGINE_PLAIN", "ENGINE_STREAM", "TUNE_ROD_KIND", "TUNE_RODS_PER_CTA", "TUNE_CHUNK_STEPS",
            "TUNE_ROWS_PER_THREAD", "TUNE_GENERIC_KERNEL", "TUNE_BALANCE",
            "library"]
@@ -163,6 +163,20 @@ class Grid:
     def sync(self, timeout_s: float = 0.0):
         _lib.check(self._L.llg_sync(self._h, timeout_s))
 
+    def loss_grad(self, n_steps: int, target=None, objective: int = 0, ckpt_every: int = 512):
+        """Loss of the window's mean loop and its pathwise gradient with respect to
+        (s_K, s_alpha, s_Ms); returns (L, grad[3]).  target: host array indexed by the global
+        sample number (objective 0)."""
+        L = C.c_double()
+        g = (C.c_double * 3)()
+        tp = None
+        if target is not None:
+            t = np.ascontiguousarray(target, dtype=np.float64)
+            tp = t.ctypes.data_as(C.POINTER(C.c_double))
+        _lib.check(self._L.llg_loop_area_grad(self._h, int(n_steps), int(objective), tp,
+                                              int(ckpt_every), C.byref(L), g))
+        return L.value, np.array(list(g))
+
     def autotune(self, trial_steps: int = 200) -> float:
         rate = C.c_double()
         _lib.check(self._L.llg_autotune(self._h, int(trial_steps), C.byref(rate)))
@@ -181,6 +195,39 @@ def run_batch(grids, max_steps: int, samples=None):
     done = (C.c_int64 * n)()
     _lib.check(L.llg_run_batch(hs, n, int(max_steps), sp, done))
     return list(done)
+
+
+def _loop_loss_function():
+    import torch
+
+    class LoopLoss(torch.autograd.Function):
+        """L(s_K, s_alpha, s_Ms) of a grid's loop window with its pathwise gradient:
+        forward sets the scale factors on the grid, restarts its ensemble (seed, n_real) and
+        evaluates the loss; backward returns grad_output times dL/ds."""
+
+        @staticmethod
+        def forward(ctx, scales, grid, seed, n_real, n_steps, target, objective, ckpt_every,
+                    mode, Tc, delta):
+            s = tuple(float(v) for v in scales.detach().cpu().tolist())
+            grid.set_scaling(mode=mode, Tc=Tc, delta=delta, scale=s)
+            grid.reset(seed, n_real)
+            L, g = grid.loss_grad(n_steps, target, objective, ckpt_every)
+            ctx.save_for_backward(torch.tensor(g, dtype=scales.dtype, device=scales.device))
+            return torch.tensor(L, dtype=scales.dtype, device=scales.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (g,) = ctx.saved_tensors
+            return (gout * g,) + (None,) * 10
+
+    return LoopLoss
+
+
+def loop_loss(scales, grid, *, seed, n_real, n_steps, target=None, objective=0, ckpt_every=512,
+              mode=1, Tc=858.0, delta=0.511):
+    """Differentiable loop loss (torch autograd) of the calibration scale factors."""
+    return _loop_loss_function().apply(scales, grid, seed, n_real, n_steps, target, objective,
+                                       ckpt_every, mode, Tc, delta)
 
 
 def loop_stats(samples: np.ndarray, H: np.ndarray, k_turn: int, mode=1, zeta=1.0, delta=0.511):

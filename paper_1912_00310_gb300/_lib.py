@@ -69,6 +69,7 @@ SIGNATURES = {
     "llg_sample_fields": (C.c_int, [_vp, _dp]),
     "llg_run_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _i64, C.POINTER(C.c_void_p),
                                 C.POINTER(C.c_int64)]),
+    "llg_loop_area_grad": (C.c_int, [_vp, _i64, C.c_int, _dp, _i64, _dp, _dp]),
     "llg_autotune": (C.c_int, [_vp, _i64, C.POINTER(C.c_double)]),
     "llg_plain_advance_noalloc": (C.c_int, [_vp, _fp, C.c_int, C.c_uint32, C.c_uint32, _i64, _i64,
                                             _fp, _vp, C.POINTER(C.c_int)]),

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <thread>
 #include <vector>
@@ -521,6 +522,137 @@ llg_status llg_set_state(llg_ctx *c, const float *m, int64_t step)
              "state copy in");
     if (!dev) LLG_CUDA(cudaStreamSynchronize(c->stream), "state copy in");
     c->step = step;
+    return LLG_OK;
+}
+
+llg_status llg_loop_area_grad(llg_ctx *c, int64_t n_steps, int objective, const double *target,
+                              int64_t ckpt_every, double *loss_out, double grad_out[3])
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (c->n_real < 1 || !c->d_m) return fail(LLG_EINVAL, "no ensemble (llg_reset first)");
+    if (n_steps < 1 || ckpt_every < 1 || ckpt_every > (1 << 20)) return fail(LLG_EINVAL, "need n_steps >= 1, 1 <= ckpt_every <= 2^20");
+    if (objective != 0 && objective != 1) return fail(LLG_EINVAL, "objective must be 0 (mismatch) or 1 (area)");
+    if (objective == 0 && !target) return fail(LLG_EINVAL, "the mismatch objective needs a target");
+    llg::Derived d;
+    llg_status s = derived_of(c, &d);
+    if (s != LLG_OK) return s;
+    DeviceGuard g(c->device);
+    llg::KParams kp = llg::kparams_of(d, c->nx, c->ny, c->nz, c->periodic, c->sw.dt);
+    kp.seed = c->seed;
+    kp.real0 = c->real0;
+    if (!llg::adjoint_supported(kp, c->device))
+        return fail(LLG_EUNSUPPORTED, "the adjoint handles rods of at most 1024 cells with free faces");
+    llg::RodPlan plan{};
+    if (!llg::rod_plan(kp, c->n_real, c->device, &plan, 1, 0, 0))
+        return fail(LLG_EUNSUPPORTED, "no resident forward plan for this grid");
+    const long long step0 = c->step, N = n_steps, C = ckpt_every;
+    const long long S = (N + C - 1) / C;
+    const long long se = d.sample_every;
+    const long long k_first = step0 / se + 1, k_last = (step0 + N) / se;
+    const long long K = k_last >= k_first ? k_last - k_first + 1 : 0;
+    if (K < 1) return fail(LLG_EINVAL, "the window holds no sample");
+    if (k_last >= d.n_samples && d.n_half > 0) return fail(LLG_EINVAL, "the window runs past the end of the loop");
+    const size_t state = (size_t)c->n_real * (size_t)ncells_of(c) * 3;
+    const long long ns_total = std::max<long long>(d.n_samples, k_last + 1);
+    float *ckpt = nullptr, *seg = nullptr, *lam = nullptr, *work = nullptr, *smp = nullptr;
+    double *w = nullptr, *partial = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(ckpt);
+        cudaFree(seg);
+        cudaFree(lam);
+        cudaFree(work);
+        cudaFree(smp);
+        cudaFree(w);
+        cudaFree(partial);
+    };
+    cudaError_t e = cudaMalloc(&ckpt, sizeof(float) * state * (size_t)S);
+    if (e == cudaSuccess) e = cudaMalloc(&seg, sizeof(float) * state * (size_t)std::min(C, N));
+    if (e == cudaSuccess) e = cudaMalloc(&lam, sizeof(float) * state);
+    if (e == cudaSuccess) e = cudaMalloc(&work, sizeof(float) * state);
+    if (e == cudaSuccess) e = cudaMalloc(&smp, sizeof(float) * (size_t)c->n_real * (size_t)ns_total);
+    if (e == cudaSuccess) e = cudaMalloc(&w, sizeof(double) * (size_t)K);
+    if (e == cudaSuccess) e = cudaMalloc(&partial, sizeof(double) * 5 * (size_t)c->n_real);
+    if (e != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return fail(LLG_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
+    }
+    llg::KParams kps = kp;
+    kps.n_samples = ns_total;
+    const cudaStream_t st = c->stream;
+    // forward pass with a checkpoint at the start of every segment
+    e = cudaMemcpyAsync(work, c->d_m, sizeof(float) * state, cudaMemcpyDeviceToDevice, st);
+    for (long long sg = 0; sg < S && e == cudaSuccess; ++sg) {
+        e = cudaMemcpyAsync(ckpt + (size_t)sg * state, work, sizeof(float) * state, cudaMemcpyDeviceToDevice, st);
+        const long long len = std::min(C, N - sg * C);
+        if (e == cudaSuccess)
+            e = llg::rod_advance(kps, plan, work, c->n_real, step0 + sg * C, len, smp, c->d_status, nullptr, st);
+    }
+    std::vector<float> hs((size_t)c->n_real * (size_t)ns_total);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hs.data(), smp, sizeof(float) * hs.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "adjoint forward");
+    }
+    // loss and its weights on the realisation-mean samples
+    std::vector<double> mbar((size_t)K, 0.0), wk((size_t)K, 0.0), Hk((size_t)K);
+    for (long long k = 0; k < K; ++k) {
+        double sum = 0.0;
+        for (int r = 0; r < c->n_real; ++r) sum += hs[(size_t)r * ns_total + (size_t)(k_first + k)];
+        mbar[(size_t)k] = sum / c->n_real;
+        const long long n = (k_first + k) * se;
+        if (d.n_half > 0) {
+            const long long ph = n % (2 * d.n_half);
+            const long long tri = ph <= d.n_half ? ph : 2 * d.n_half - ph;
+            Hk[(size_t)k] = c->sw.H_start_Oe + (c->sw.H_turn_Oe - c->sw.H_start_Oe) * ((double)tri / (double)d.n_half);
+        } else {
+            Hk[(size_t)k] = c->sw.H_start_Oe;
+        }
+    }
+    double L = 0.0;
+    if (objective == 0) {
+        for (long long k = 0; k < K; ++k) {
+            const double err = mbar[(size_t)k] - target[k_first + k];
+            L += err * err / (double)K;
+            wk[(size_t)k] = 2.0 * err / (double)K;
+        }
+    } else {
+        // signed trapezoid area of the window's mean loop, sum (m_k + m_k+1)/2 (H_k+1 - H_k)
+        for (long long k = 0; k + 1 < K; ++k) {
+            const double dH = Hk[(size_t)k + 1] - Hk[(size_t)k];
+            L += 0.5 * (mbar[(size_t)k] + mbar[(size_t)k + 1]) * dH;
+            wk[(size_t)k] += 0.5 * dH;
+            wk[(size_t)k + 1] += 0.5 * dH;
+        }
+    }
+    e = cudaMemcpyAsync(w, wk.data(), sizeof(double) * (size_t)K, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lam, 0, sizeof(float) * state, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(partial, 0, sizeof(double) * 5 * (size_t)c->n_real, st);
+    for (long long sg = S - 1; sg >= 0 && e == cudaSuccess; --sg) {
+        const long long len = std::min(C, N - sg * C);
+        e = llg::adjoint_segment(kps, c->n_real, step0 + sg * C, (int)len, step0 + N, k_first, (int)K,
+                                 ckpt + (size_t)sg * state, seg, lam, w, partial, st);
+    }
+    std::vector<double> hp((size_t)c->n_real * 5);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hp.data(), partial, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint backward");
+    double gs[5] = {0, 0, 0, 0, 0};
+    for (int r = 0; r < c->n_real; ++r)
+        for (int k = 0; k < 5; ++k) gs[k] += hp[(size_t)r * 5 + k];
+    // chain rule to the scale factors: alpha = alpha0 s_alpha (in the torque, in a = dt g1 with
+    // g1 = g0/(1 + alpha^2), and in sigma ~ sqrt(alpha / Ms)); c_ex ~ 1/s_Ms; c_an ~ s_K/s_Ms
+    const double alpha = d.alpha, a = c->sw.dt * d.g1;
+    const double da_dalpha = -2.0 * alpha * a / (1.0 + alpha * alpha);
+    const double sK = c->sc.sK, sA = c->sc.sAlpha, sM = c->sc.sMs;
+    grad_out[0] = gs[3] * d.c_an / sK;
+    grad_out[1] = (gs[0] + gs[1] * da_dalpha) * (alpha / sA) + gs[4] / (2.0 * sA);
+    grad_out[2] = -(gs[2] * d.c_ex + gs[3] * d.c_an) / sM - gs[4] / (2.0 * sM);
+    if (loss_out) *loss_out = L;
     return LLG_OK;
 }
 

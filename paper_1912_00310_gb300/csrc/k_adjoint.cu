@@ -1,0 +1,270 @@
+// k_adjoint.cu -- pathwise adjoint of the stochastic Heun step of Eq. 1: the gradient of a loss of
+// the sampled M(H) loop with respect to the calibration scale factors (s_K, s_alpha, s_Ms) with
+// the thermal normals held fixed (the same Philox draws replayed).
+//
+// Forward (per cell i, step n; N_i(m) = sum of the neighbours' m):
+//   H  = c_ex N(m) + (c_an m_z + h_n) z + sigma xi          c0 = m x H,  s0 = c0 + alpha m x c0
+//   p  = m - a s0,  m~ = p/|p|                              (a = dt g1, g1 = g0/(1 + alpha^2))
+//   H~ = c_ex N(m~) + (c_an m~_z + h_n+1) z + sigma xi       c1 = m~ x H~, s1 = c1 + alpha m~ x c1
+//   q  = m - (a/2)(s0 + s1),  m' = q/|q|
+// Reverse (given g' = dL/dm'):
+//   g_q = (g' - m'(m'.g'))/|q|;  g_m = g_q;  g_s0 = g_s1 = -(a/2) g_q;  g_a += -(s0 + s1).g_q/2
+//   through s1: g_c1 = g_s1 + alpha g_s1 x m~;  g_m~ = alpha c1 x g_s1 + H~ x g_c1;
+//               g_H~ = g_c1 x m~;  g_alpha += (m~ x c1).g_s1
+//   through H~: g_m~_i += c_ex sum_j g_H~_j (neighbours), g_m~_z += c_an g_H~_z;
+//               g_cex += g_H~.N(m~), g_can += g_H~_z m~_z, g_sigma += g_H~.xi
+//   g_p = (g_m~ - m~(m~.g_m~))/|p|;  g_m += g_p;  g_s0 += -a g_p;  g_a += -s0.g_p
+//   through s0 and H: as through s1 and H~, with m, c0, H
+// and dL/dm of the previous state is g_m.  The host maps (g_alpha, g_a, g_cex, g_can, g_sigma)
+// to the scale factors (g_sigma is accumulated as g_H.h_th, i.e. sigma dL/dsigma).
+//
+// One CTA per rod, one cell per thread, the rod in shared memory with a zero ghost layer.  A
+// launch handles one checkpoint segment: it first recomputes the segment's states forward from
+// the checkpoint (bitwise the forward run: same arithmetic), storing them in global scratch
+// (L2-resident for the calibration workload), then walks them backward.  Parameter partial sums
+// are FP64 per thread and per CTA.
+#include <cmath>
+
+#include "llg_internal.h"
+#include "physics.cuh"
+
+namespace llg {
+namespace {
+
+__device__ __forceinline__ float3 cross3(float3 a, float3 b)
+{
+    return make_float3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 scale3(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 zero3a() { return make_float3(0.f, 0.f, 0.f); }
+
+struct AdjParams {
+    KParams p;
+    long long seg_start;  // first step of the segment
+    int seg_len;          // steps in the segment
+    long long win_end;    // last step index + 1 of the window (samples at (start, win_end])
+    long long k_first;    // sample number of w[0]
+    int n_k;
+    float inj_scale;      // 1 / (n_real * ncells)
+};
+
+// Neighbour sum over the six faces (x-, x+, y-, y+, z-, z+) of a ghost-padded rod.
+__device__ __forceinline__ float3 nsum(const float4 *A, int q, int sy, int sz)
+{
+    float3 nb = add3(xyz(A[q - 1]), xyz(A[q + 1]));
+    nb = add3(nb, xyz(A[q - sy]));
+    nb = add3(nb, xyz(A[q + sy]));
+    nb = add3(nb, xyz(A[q - sz]));
+    return add3(nb, xyz(A[q + sz]));
+}
+
+__global__ void __launch_bounds__(1024) adjoint_segment_kernel(
+    AdjParams ap, const float *__restrict__ ckpt, float *__restrict__ seg, float *__restrict__ lam,
+    const double *__restrict__ w, double *__restrict__ partial)
+{
+    extern __shared__ float4 sm4[];
+    const KParams &p = ap.p;
+    const int px = p.nx + 2, py = p.ny + 2;
+    const int sy = px, sz = px * py;
+    const int rod_pad = sz * (p.nz + 2);
+    float4 *M = sm4, *P = M + rod_pad, *GT = P + rod_pad, *GH = GT + rod_pad;
+    const int rod = blockIdx.x;
+    const int ncell = p.ncells;
+    const int c = threadIdx.x;
+    const bool act = c < ncell;
+    for (int i = threadIdx.x; i < 4 * rod_pad; i += blockDim.x) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int q = 0;
+    if (act) {
+        const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
+        q = (x + 1) + sy * (y + 1) + sz * (z + 1);
+    }
+    const uint32_t real = p.real0 + (uint32_t)rod;
+    const size_t state = (size_t)ncell * 3;
+    const size_t rod_off = (size_t)rod * state;
+    const int n_rods = gridDim.x;
+    float3 m = zero3a();
+    if (act) m = make_float3(ckpt[rod_off + 3 * c], ckpt[rod_off + 3 * c + 1], ckpt[rod_off + 3 * c + 2]);
+    __syncthreads();
+
+    // ---- forward recomputation of the segment: seg[j] = state before step seg_start + j ----
+    Triangle field;
+    field.init(ap.seg_start, p.n_half, p.H0, p.slope);
+    float Hn = field.value();
+    for (int j = 0; j < ap.seg_len; ++j) {
+        const unsigned long long n = (unsigned long long)(ap.seg_start + j);
+        field.inc();
+        const float Hn1 = field.value();
+        float *sj = seg + (size_t)j * n_rods * state + rod_off;
+        float3 acc = zero3a(), h = zero3a();
+        if (act) {
+            sj[3 * c] = m.x;
+            sj[3 * c + 1] = m.y;
+            sj[3 * c + 2] = m.z;
+            M[q] = pad4(m);
+        }
+        __syncthreads();
+        if (act) {
+            h = thermal_field(p.seed, real, (uint32_t)c, n, p.sigma);
+            const float3 H = effective_field(nsum(M, q, sy, sz), m, h, p.c_ex, p.c_an, Hn);
+            const float3 s0 = llg_torque(m, H, p.alpha);
+            P[q] = pad4(normalised(axpy(p.neg_dt_g1, s0, m)));
+            acc = axpy(p.neg_hdt_g1, s0, m);
+        }
+        __syncthreads();
+        if (act) {
+            const float3 t = xyz(P[q]);
+            const float3 H = effective_field(nsum(P, q, sy, sz), t, h, p.c_ex, p.c_an, Hn1);
+            m = normalised(axpy(p.neg_hdt_g1, llg_torque(t, H, p.alpha), acc));
+        }
+        __syncthreads();
+        Hn = Hn1;
+    }
+
+    // ---- backward through the segment ----
+    float3 g = zero3a();  // dL/d(state after the step being reversed)
+    if (act) g = make_float3(lam[rod_off + 3 * c], lam[rod_off + 3 * c + 1], lam[rod_off + 3 * c + 2]);
+    double g_alpha = 0.0, g_a = 0.0, g_cex = 0.0, g_can = 0.0, g_sigma = 0.0;
+    const float a = -p.neg_dt_g1;  // dt g1
+    const float ha = -p.neg_hdt_g1;
+    const float alpha = p.alpha;
+    field.init(ap.seg_start + ap.seg_len - 1, p.n_half, p.H0, p.slope);
+    for (int j = ap.seg_len - 1; j >= 0; --j) {
+        const long long n = ap.seg_start + j;
+        const float hn = field.value();
+        Triangle f1 = field;
+        f1.inc();
+        const float hn1 = f1.value();
+        // loss gradient of the state after step n, if it is a sample of the window
+        const long long done = n + 1;
+        if (p.sample_every > 0 && done % p.sample_every == 0 && done <= ap.win_end) {
+            const long long k = done / p.sample_every - ap.k_first;
+            if (k >= 0 && k < ap.n_k) g.z += (float)w[k] * ap.inj_scale;
+        }
+        const float *sj = seg + (size_t)j * n_rods * state + rod_off;
+        float3 mi = zero3a(), h = zero3a(), H = zero3a(), c0 = zero3a(), s0 = zero3a(), t = zero3a();
+        float pn = 1.f;
+        if (act) {
+            mi = make_float3(sj[3 * c], sj[3 * c + 1], sj[3 * c + 2]);
+            M[q] = pad4(mi);
+        }
+        __syncthreads();
+        float3 Nm = zero3a();
+        if (act) {
+            h = thermal_field(p.seed, real, (uint32_t)c, (unsigned long long)n, p.sigma);
+            Nm = nsum(M, q, sy, sz);
+            H = effective_field(Nm, mi, h, p.c_ex, p.c_an, hn);
+            c0 = cross3(mi, H);
+            s0 = llg_torque(mi, H, alpha);
+            const float3 pv = axpy(p.neg_dt_g1, s0, mi);
+            pn = sqrtf(dot3(pv, pv));
+            t = normalised(pv);
+            P[q] = pad4(t);
+        }
+        __syncthreads();
+        float3 gHt = zero3a(), Nt = zero3a(), c1 = zero3a(), gq = zero3a(), gmt = zero3a(), Ht = zero3a();
+        float3 s1 = zero3a();
+        if (act) {
+            Nt = nsum(P, q, sy, sz);
+            Ht = effective_field(Nt, t, h, p.c_ex, p.c_an, hn1);
+            c1 = cross3(t, Ht);
+            s1 = llg_torque(t, Ht, alpha);
+            const float3 qv = axpy(p.neg_hdt_g1, add3(s0, s1), mi);
+            const float qn = sqrtf(dot3(qv, qv));
+            const float3 mp = scale3(1.f / qn, qv);
+            gq = scale3(1.f / qn, sub3(g, scale3(dot3(mp, g), mp)));
+            const float3 gs1 = scale3(-ha, gq);
+            g_a += -0.5 * (double)dot3(add3(s0, s1), gq);
+            const float3 gc1 = add3(gs1, scale3(alpha, cross3(gs1, t)));
+            gmt = add3(scale3(alpha, cross3(c1, gs1)), cross3(Ht, gc1));
+            gHt = cross3(gc1, t);
+            g_alpha += (double)dot3(cross3(t, c1), gs1);
+            GT[q] = pad4(gHt);
+        }
+        __syncthreads();
+        float3 gH = zero3a(), gm = zero3a();
+        if (act) {
+            gmt = axpy(p.c_ex, nsum(GT, q, sy, sz), gmt);
+            gmt.z = fmaf(p.c_an, gHt.z, gmt.z);
+            g_cex += (double)dot3(gHt, Nt);
+            g_can += (double)gHt.z * (double)t.z;
+            g_sigma += (double)dot3(gHt, h);  // d/dsigma = (1/sigma) g_H.h, divided on the host
+            const float3 gp = scale3(1.f / pn, sub3(gmt, scale3(dot3(t, gmt), t)));
+            gm = add3(gq, gp);                                     // q = m - ..., p = m - a s0
+            const float3 gs0 = add3(scale3(-ha, gq), scale3(-a, gp));  // from q and from p
+            g_a += -(double)dot3(s0, gp);
+            const float3 gc0 = add3(gs0, scale3(alpha, cross3(gs0, mi)));
+            gm = add3(gm, add3(scale3(alpha, cross3(c0, gs0)), cross3(H, gc0)));
+            gH = cross3(gc0, mi);
+            g_alpha += (double)dot3(cross3(mi, c0), gs0);
+            GH[q] = pad4(gH);
+        }
+        __syncthreads();
+        if (act) {
+            gm = axpy(p.c_ex, nsum(GH, q, sy, sz), gm);
+            gm.z = fmaf(p.c_an, gH.z, gm.z);
+            g_cex += (double)dot3(gH, Nm);
+            g_can += (double)gH.z * (double)mi.z;
+            g_sigma += (double)dot3(gH, h);
+            g = gm;
+        }
+        __syncthreads();
+        // step back the field phase
+        if (p.n_half > 0) field.ph = (field.ph == 0 ? 2 * p.n_half : field.ph) - 1;
+    }
+    if (act) {
+        lam[rod_off + 3 * c] = g.x;
+        lam[rod_off + 3 * c + 1] = g.y;
+        lam[rod_off + 3 * c + 2] = g.z;
+    }
+    // per-CTA partial sums of the parameter adjoints, fixed order
+    __shared__ double red[5][32];
+    double v[5] = {g_alpha, g_a, g_cex, g_can, g_sigma};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double s = 0.0;
+        for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) s += red[threadIdx.x][wi];
+        partial[(size_t)rod * 5 + threadIdx.x] += s;
+    }
+}
+
+}  // namespace
+
+bool adjoint_supported(const KParams &p, int dev)
+{
+    int smem_optin = 0;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    const size_t rod_pad = (size_t)(p.nx + 2) * (p.ny + 2) * (p.nz + 2);
+    return p.periodic == 0 && p.ncells <= 1024 && 4 * rod_pad * sizeof(float4) <= (size_t)smem_optin;
+}
+
+cudaError_t adjoint_segment(const KParams &p, int n_real, long long seg_start, int seg_len, long long win_end,
+                            long long k_first, int n_k, const float *ckpt, float *seg, float *lam,
+                            const double *w, double *partial, cudaStream_t st)
+{
+    AdjParams ap;
+    ap.p = p;
+    ap.seg_start = seg_start;
+    ap.seg_len = seg_len;
+    ap.win_end = win_end;
+    ap.k_first = k_first;
+    ap.n_k = n_k;
+    ap.inj_scale = 1.0f / ((float)n_real * (float)p.ncells);
+    const size_t rod_pad = (size_t)(p.nx + 2) * (p.ny + 2) * (p.nz + 2);
+    const size_t smem = 4 * rod_pad * sizeof(float4);
+    cudaError_t e = cudaFuncSetAttribute(adjoint_segment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int threads = (p.ncells + 31) / 32 * 32;
+    adjoint_segment_kernel<<<n_real, threads, smem, st>>>(ap, ckpt, seg, lam, w, partial);
+    return cudaGetLastError();
+}
+
+}  // namespace llg

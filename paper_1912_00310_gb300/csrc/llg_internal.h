@@ -107,6 +107,15 @@ cudaError_t slab_advance(const KParams &p, const SlabPlan &plan, float *m, int n
                          float *partial, cudaStream_t st, long long *launches);
 size_t slab_partial_floats(int n_real);
 
+// ---- adjoint (k_adjoint.cu): one launch per checkpoint segment, rods of at most 1024 cells -----
+bool adjoint_supported(const KParams &p, int dev);
+// ckpt: state at seg_start; seg: scratch of seg_len states; lam: dL/d(state at seg_start +
+// seg_len) in, dL/d(state at seg_start) out; w: loss weights of the window's samples k_first..;
+// partial: [n_real][5] FP64 accumulators (g_alpha, g_a, g_cex, g_can, sigma g_sigma).
+cudaError_t adjoint_segment(const KParams &p, int n_real, long long seg_start, int seg_len, long long win_end,
+                            long long k_first, int n_k, const float *ckpt, float *seg, float *lam,
+                            const double *w, double *partial, cudaStream_t st);
+
 // ---- host runtime helpers (api.cpp) ---------------------------------------------------------
 // Store a message for llg_last_error() on this thread.
 void set_last_error(const char *msg);

@@ -1,0 +1,121 @@
+"""GPU pathwise adjoint (llg_loop_area_grad) against the FP64 forward-mode oracle gradient and
+against central finite differences with common random numbers, within 1e-2 relative."""
+import numpy as np
+import pytest
+
+from workloads import CONFIGS, MAGNETITE as M, ROD_DIMS, random_unit_state
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1912_00310_gb300 import build
+    build.build()
+    import paper_1912_00310_gb300 as P
+    return P
+
+
+def grid(pkg, dims, scale=(1.0, 1.0, 1.0), alpha=None):
+    g = pkg.Grid(*dims, a0=M["a0"], b=4)
+    g.set_material(A0=M["A0"], Ms=M["Ms"], K0=M["K0"], alpha=alpha or M["alpha"], T=M["T"])
+    g.set_scaling(mode=1, Tc=M["Tc"], scale=scale)
+    g.set_sweep(H_start=1500.0, H_turn=-1500.0, rate=1000.0, dt=10e-15, sample_dH=1.0)
+    return g
+
+
+def target_for(g):
+    return 0.92 + 0.05 * np.cos(np.arange(g.n_samples) / 7.0)
+
+
+def oracle_grad(orc, dims, m0, scale, step0, n_steps, target, alpha=None, seed=0):
+    p = orc.material_problem(*dims, a0=M["a0"], b=4, A0=M["A0"], K0=M["K0"], Ms=M["Ms"],
+                             alpha=alpha or M["alpha"], T=M["T"], dt=10e-15, mode=1, Tc=M["Tc"],
+                             H_start_Oe=1500.0, H_turn_Oe=-1500.0, rate_Oe_per_ns=1000.0)
+    return orc.loss_grad(p, m0, target=target, scale=scale, seed=seed, step0=step0,
+                         n_steps=n_steps, sample_every=100)
+
+
+@pytest.mark.parametrize("scale,alpha", [((1.0, 1.0, 1.0), None), ((1.25, 0.8, 1.1), 0.5)])
+def test_adjoint_matches_oracle_gradient_tiny_grid(pkg, orc, scale, alpha):
+    dims, n_real, step0, n_steps = (1, 2, 3), 16, 300, 2000
+    g = grid(pkg, dims, scale, alpha)
+    g.reset(seed=0, n_real=n_real)
+    m0 = random_unit_state(n_real, 6, seed=21, cone=0.6)
+    g.set_state(m0.astype(np.float32), step0)
+    target = target_for(g)
+    L, grad = g.loss_grad(n_steps, target, objective=0, ckpt_every=512)  # 4 segments, last ragged
+    Lo, go, _ = oracle_grad(orc, dims, m0.astype(np.float32).astype(np.float64), scale, step0,
+                            n_steps, target, alpha)
+    assert L == pytest.approx(Lo, rel=1e-3)
+    for k in range(3):
+        assert grad[k] == pytest.approx(go[k], rel=1e-2, abs=1e-3 * np.abs(go).max()), (k, grad, go)
+    assert g.step == step0  # the ensemble was not advanced
+    g.close()
+
+
+def test_adjoint_matches_central_differences(pkg):
+    """Central differences of the GPU forward loss (same noise at +-h), FP32, h = 1e-2."""
+    dims, n_real, n_steps = ROD_DIMS[4], 8, 3000
+    g = grid(pkg, dims)
+    target = target_for(g)
+    base = np.array([1.0, 1.0, 1.0])
+    g.reset(seed=4, n_real=n_real)
+    _, grad = g.loss_grad(n_steps, target, 0, 256)
+    for k in range(3):
+        h = 1e-2
+        vals = []
+        for sgn in (1, -1):
+            s = base.copy()
+            s[k] += sgn * h
+            g.set_scaling(mode=1, Tc=M["Tc"], scale=tuple(s))
+            g.reset(seed=4, n_real=n_real)
+            vals.append(g.loss_grad(n_steps, target, 0, 256)[0])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert grad[k] == pytest.approx(fd, rel=3e-2, abs=1e-2 * np.abs(grad).max()), (k, grad[k], fd)
+        g.set_scaling(mode=1, Tc=M["Tc"], scale=tuple(base))
+    g.close()
+
+
+def test_adjoint_full_rod_vs_oracle(pkg, orc):
+    """The b = 4 rod (168 cells), 4 realisations from +z, a 3000-step window: GPU adjoint vs the
+    FP64 forward-mode gradient; and the area objective against the oracle's forward loss."""
+    dims, n_real, n_steps = ROD_DIMS[4], 4, 3000
+    g = grid(pkg, dims)
+    g.reset(seed=0, n_real=n_real)
+    target = target_for(g)
+    L, grad = g.loss_grad(n_steps, target, 0, 512)
+    m0 = orc.uniform_state(n_real, g.ncells)
+    Lo, go, _ = oracle_grad(orc, dims, m0, (1.0, 1.0, 1.0), 0, n_steps, target)
+    assert L == pytest.approx(Lo, rel=1e-3)
+    assert np.allclose(grad, go, rtol=1e-2, atol=1e-3 * np.abs(go).max()), (grad, go)
+    g.close()
+
+
+def test_calibration_workload_launch_shape(pkg):
+    """The calibration workload: b = 4 rod, 64 realisations, 20k-step window at 1000 Oe/ns,
+    checkpoints every 512 steps; finite gradient, loss equal to a plain forward run's, and the
+    autograd wrapper returning the same gradient."""
+    cfg = CONFIGS["adjoint_b4"]
+    g = grid(pkg, cfg["dims"])
+    g.reset(seed=cfg["seed"], n_real=cfg["n_real"])
+    target = target_for(g)
+    L, grad = g.loss_grad(cfg["window_steps"], target, 0, cfg["ckpt_every"])
+    assert np.all(np.isfinite(grad)) and np.isfinite(L)
+    S = torch.zeros((cfg["n_real"], g.n_samples), device="cuda")
+    g.reset(seed=cfg["seed"], n_real=cfg["n_real"])
+    g.advance(cfg["window_steps"], S)
+    g.sync(120)
+    mbar = S[:, 1:cfg["window_steps"] // 100 + 1].double().mean(0).cpu().numpy()
+    Lf = float(np.mean((mbar - target[1:len(mbar) + 1]) ** 2))
+    assert L == pytest.approx(Lf, rel=1e-6)
+    import paper_1912_00310_gb300 as P
+    s = torch.tensor([1.0, 1.0, 1.0], dtype=torch.float64, requires_grad=True)
+    loss = P.loop_loss(s, g, seed=cfg["seed"], n_real=cfg["n_real"], n_steps=cfg["window_steps"],
+                       target=target, ckpt_every=cfg["ckpt_every"], Tc=M["Tc"])
+    loss.backward()
+    assert float(loss) == pytest.approx(L, rel=1e-12)
+    assert np.allclose(s.grad.numpy(), grad, rtol=1e-12)
+    g.close()
