@@ -351,6 +351,7 @@ def side_measurements(args, torch, pkg, cfg, g, samples, S_per_step, flush):
                                   "resident_over_plain": None}
     out["ladder_batch"] = ladder_batch(args, torch, pkg, flush)
     out["slab_512x512x56"] = slab_stream(args, torch, pkg, flush)
+    out["adjoint_b4"] = adjoint_calibration(args, torch, pkg)
     out["small_rod_b4_4real"] = {
         "resident_cell_steps_per_s": res["resident"], "plain_cell_steps_per_s": res["plain"],
         "resident_over_plain": res["resident"] / res["plain"],
@@ -452,6 +453,54 @@ def slab_stream(args, torch, pkg, flush):
             "hbm_peak_basis": basis, "hbm_frac_algorithmic": alg / peak,
             "alu_frac": ALU_OPS_PER_CELL_STEP * rate / (152 * ALU_LANES_PER_SM * MAX_SM_MHZ * 1e6),
             "l2": "state (470 MB ping-pong) larger than L2"}
+
+
+def adjoint_calibration(args, torch, pkg):
+    """Gradient evaluations per second of the calibration workload: b = 4 rod, 64 realisations,
+    a 20k-step window at 1000 Oe/ns, checkpoints every 512 steps, mismatch against a fixed loop
+    (the same window's mean loop of the b = 1 rod, 64 realisations)."""
+    import numpy as np
+    from workloads import CONFIGS, DT_BY_B, MAGNETITE as M, ROD_DIMS
+    c5 = CONFIGS["adjoint_b4"]
+    # target: the b = 1 rod's mean loop over the same field window
+    t1 = pkg.Grid(*ROD_DIMS[1], a0=M["a0"], b=1)
+    t1.set_material(A0=M["A0"], Ms=M["Ms"], K0=M["K0"], alpha=M["alpha"], T=M["T"])
+    t1.set_scaling(mode=c5["mode"], Tc=M["Tc"])
+    t1.set_sweep(H_start=c5["H_start"], H_turn=c5["H_turn"], rate=c5["rate"], dt=DT_BY_B[1], sample_dH=1.0)
+    t1.set_engine(pkg.ENGINE_RESIDENT)
+    t1.reset(seed=c5["seed"] + 1, n_real=c5["n_real"])
+    S1 = torch.zeros((c5["n_real"], t1.n_samples), device="cuda")
+    S1[:, 0] = 1.0
+    window_oe = c5["window_steps"] * c5["rate"] * 1e9 * c5["dt"]
+    t1.advance(int(round(window_oe / (c5["rate"] * 1e9 * DT_BY_B[1]))), S1)
+    t1.sync(600)
+    target = S1.double().mean(0).cpu().numpy()
+    t1.close()
+    g = pkg.Grid(*c5["dims"], a0=M["a0"], b=c5["b"])
+    g.set_material(A0=M["A0"], Ms=M["Ms"], K0=M["K0"], alpha=M["alpha"], T=M["T"])
+    g.set_scaling(mode=c5["mode"], Tc=M["Tc"])
+    g.set_sweep(H_start=c5["H_start"], H_turn=c5["H_turn"], rate=c5["rate"], dt=c5["dt"], sample_dH=1.0)
+    g.set_engine(pkg.ENGINE_RESIDENT)
+    g.reset(seed=c5["seed"], n_real=c5["n_real"])
+    tgt = np.zeros(g.n_samples)
+    tgt[:len(target)] = target[:g.n_samples]
+    g.loss_grad(c5["window_steps"], tgt, 0, c5["ckpt_every"])  # warm-up
+    t0 = time.perf_counter()
+    n_eval = max(1, args.steps)
+    for _ in range(n_eval):
+        L, grad = g.loss_grad(c5["window_steps"], tgt, 0, c5["ckpt_every"])
+    t_grad = (time.perf_counter() - t0) / n_eval
+    S = torch.zeros((c5["n_real"], g.n_samples), device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.advance(c5["window_steps"], S)
+    g.sync(600)
+    t_fwd = time.perf_counter() - t0
+    g.close()
+    return {"grads_per_s": 1.0 / t_grad, "s_per_grad": t_grad, "forward_only_s": t_fwd,
+            "grad_over_forward": t_grad / t_fwd, "loss": L, "grad": [float(x) for x in grad],
+            "cell_steps_per_grad": c5["n_real"] * math.prod(c5["dims"]) * c5["window_steps"],
+            "timing": "host wall clock per synchronous llg_loop_area_grad call"}
 
 
 def profile_case(name):
