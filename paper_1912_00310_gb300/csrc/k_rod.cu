@@ -362,10 +362,22 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_ker
 // of a step is unrolled, so the plane windows rotate by register renaming and the slot parity
 // is a constant.  Same schedule and arithmetic as rod_pipelined_kernel.
 // ------------------------------------------------------------------------------------------
-template <int R, int NX>
+// NY, NZ > 0: the rod's y and z extents are compile-time constants (the b = 1 rod), so every
+// shared-memory offset of the stencil is an immediate.
+template <int R, int NX, int NY = 0, int NZ = 0>
 struct PipelinedRod {
     float4 *M, *S;
-    int ny, PL, ncell;
+    int ny_rt, PL_rt, ncell;
+    __device__ __forceinline__ int ny() const
+    {
+        if constexpr (NY > 0) return NY;
+        return ny_rt;
+    }
+    __device__ __forceinline__ int PL() const
+    {
+        if constexpr (NY > 0 && NZ > 0) return (NZ + 2) * NY;
+        return PL_rt;
+    }
     int q[R];
     float wm[R], wp[R];
     bool act[R];
@@ -373,11 +385,12 @@ struct PipelinedRod {
 
     __device__ void setup(float4 *sm, const KParams &p)
     {
-        ny = p.ny;
-        PL = (p.nz + 2) * ny;
+        ny_rt = p.ny;
+        PL_rt = (p.nz + 2) * p.ny;
         ncell = p.ncells;
         M = sm;
-        S = sm + NX * PL;
+        S = sm + NX * PL();
+        const int ny = this->ny();
         const int rows = ny * p.nz;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
@@ -397,6 +410,7 @@ struct PipelinedRod {
     __device__ __forceinline__ void sample(const KParams &p, int rod, long long k, float *__restrict__ samples,
                                         int *__restrict__ status)
     {
+        const int ny = this->ny(), PL = this->PL();
         if (k < p.n_samples && threadIdx.x < 32) {
             const int lane = threadIdx.x;
             float part = 0.f;
@@ -415,6 +429,7 @@ struct PipelinedRod {
     __device__ __forceinline__ void run(const KParams &p, float *__restrict__ m_glob, int rod, long long s0,
                                         long long ns, float *__restrict__ samples, int *__restrict__ status)
     {
+        const int ny = this->ny(), PL = this->PL();
         {
             const float *g = m_glob + (size_t)rod * ncell * 3;
             for (int c = threadIdx.x; c < ncell; c += blockDim.x)
@@ -578,7 +593,7 @@ struct BalancedSchedule {
 
 // balanced == 0: one rod per CTA over [step0, step0 + n_steps).
 // balanced == 1: the segments of `sched`; needs all CTAs co-resident (cooperative launch).
-template <int R, int NX>
+template <int R, int NX, int NY = 0, int NZ = 0>
 __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_kernel(
     KParams p, float *__restrict__ m_glob, long long step0, int n_steps, float *__restrict__ samples,
     int *__restrict__ status, unsigned *__restrict__ flags, int balanced,
@@ -588,7 +603,7 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_
     extern __shared__ float4 sm4[];
     const int PL = (p.nz + 2) * p.ny;
     for (int i = threadIdx.x; i < (NX + 2) * PL; i += blockDim.x) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    PipelinedRod<R, NX> w;
+    PipelinedRod<R, NX, NY, NZ> w;
     w.setup(sm4, p);
     __syncthreads();
     __shared__ int go;
@@ -717,12 +732,12 @@ static void balanced_schedule(int n_real, int N, int G, BalancedSchedule *sc)
 
 // Launch of the nx-specialised kernel: balanced over a co-resident grid when the rods do not
 // divide evenly into waves, else one rod per CTA.
-template <int R, int NX>
+template <int R, int NX, int NY = 0, int NZ = 0>
 static cudaError_t launch_nx(const KParams &p, const RodPlan &plan, float *m, int n_real, long long step0,
                              long long n_steps, float *samples, int *status, unsigned *flags,
                              cudaStream_t st)
 {
-    auto kern = rod_pipelined_nx_kernel<R, NX>;
+    auto kern = rod_pipelined_nx_kernel<R, NX, NY, NZ>;
     cudaError_t e = set_smem(kern, plan.smem_bytes);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, per_sm = 0;
@@ -772,7 +787,9 @@ cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_r
     } else if (plan.kind == 2) {
 #define LLG_PIPELINED(R)                                                                        \
     case R:                                                                                     \
-        if (p.nx == 8 && !plan.generic) {                                                       \
+        if (p.nx == 8 && p.ny == 24 && p.nz == 56 && !plan.generic) {                           \
+            e = launch_nx<R, 8, 24, 56>(p, plan, m, n_real, step0, n_steps, samples, status, flags, st); \
+        } else if (p.nx == 8 && !plan.generic) {                                                \
             e = launch_nx<R, 8>(p, plan, m, n_real, step0, n_steps, samples, status, flags, st); \
         } else {                                                                                \
             e = set_smem(rod_pipelined_kernel<R>, plan.smem_bytes);                             \

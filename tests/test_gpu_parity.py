@@ -129,10 +129,12 @@ def test_engines_bitwise_equal(pkg, dims, b, n_real):
         assert torch.equal(sm[:, 1:4], outs[0][1][:, 1:4])
 
 
-def test_b1_kernel_variants_bitwise_equal(pkg):
-    """The b = 1 rod: the plane-count-specialised kernel and the runtime-size kernel, with 2, 3
-    and 4 rows per thread, give bitwise-equal states and samples over several sample intervals."""
-    dims, b, dt, n_real = ROD_DIMS[1], 1, 2e-15, 3
+@pytest.mark.parametrize("dims", [ROD_DIMS[1], (8, 40, 30)])
+def test_b1_kernel_variants_bitwise_equal(pkg, dims):
+    """Rods with 8 x planes: the kernels specialised for the plane count (and, for the 8x24x56
+    rod, for the whole shape) and the runtime-size kernel, with 2, 3 and 4 rows per thread, give
+    bitwise-equal states and samples over several sample intervals."""
+    b, dt, n_real = 1, 2e-15, 3
     outs = []
     for generic in (0, 1):
         for rows in (2, 3, 4):
