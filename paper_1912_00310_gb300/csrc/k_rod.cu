@@ -452,6 +452,10 @@ struct PipelinedRod {
         float Hprev = Hs;           // field at step s (the end of step s - 1), for its corrector
         const long long se = p.sample_every;
         long long next_sample = (samples && se > 0) ? (s0 / se + 1) * se : -1;
+        // thermal field of the next predictor, drawn one iteration ahead (before the barrier)
+        float3 hpre[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) hpre[j] = thermal_field(keys, cbase[j], (unsigned long long)s0, p.sigma);
 
         for (long long s = 0; s < ns; ++s) {
             const unsigned long long n = (unsigned long long)(s0 + s);
@@ -470,7 +474,7 @@ struct PipelinedRod {
                         mB[j] = xyz(Mp[qq]);
                     }
                     const float3 mnext = x + 1 < NX ? xyz(Mp[qq + PL]) : zero3();
-                    hnew[j] = thermal_field(keys, cbase[j] + (uint32_t)x, n, p.sigma);
+                    hnew[j] = hpre[j];
                     float3 nb = add3(mA[j], mnext);
                     nb = axpy(wm[j], xyz(Mp[qq - 1]), nb);
                     nb = axpy(wp[j], xyz(Mp[qq + 1]), nb);
@@ -511,6 +515,9 @@ struct PipelinedRod {
                     tB[j] = tnew[j];
                     acc[j] = anew[j];
                     hth[j] = hnew[j];
+                    // the next predictor: plane x+1 of this step, or plane 0 of the next one
+                    hpre[j] = x + 1 < NX ? thermal_field(keys, cbase[j] + (uint32_t)(x + 1), n, p.sigma)
+                                         : thermal_field(keys, cbase[j], n + 1, p.sigma);
                 }
                 __syncthreads();
                 if (x == 0 && s > 0 && s0 + s == next_sample) {
@@ -677,9 +684,9 @@ bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_ki
     if (bytes > (size_t)smem_optin) return false;
     int R = force_rows;
     if (R == 0) {
-        // fewest rows per thread that fit (two rows per thread for the b = 1 rod's 1344 rows:
-        // 672 threads measured ahead of 448 x 3 rows on GB300)
-        R = rows <= 768 ? 1 : (rows <= 1344 ? 2 : (rows <= 1536 ? 3 : 4));
+        // three rows per thread for the b = 1 rod's 1344 rows (448 threads, 128 registers):
+        // measured ahead of 672 x 2 rows (which spill at 80 registers) on GB300
+        R = rows <= 768 ? 1 : (rows <= 1536 ? 3 : 4);
     }
     if (R < 1 || R > 4 || (rows + R - 1) / R > pipelined_max_threads(R)) return false;
     plan->kind = 2;
