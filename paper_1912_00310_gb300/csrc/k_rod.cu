@@ -93,6 +93,10 @@ __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, fl
     long long next_sample = (samples && se > 0) ? (step0 / se + 1) * se : -1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = T >> 5;
 
+    // thermal field of the next step, drawn before the barrier that ends the current one
+    float3 hpre[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) hpre[k] = thermal_field(p.seed, real[k], cell[k], (unsigned long long)step0, p.sigma);
     for (long long s = 0; s < n_steps; ++s) {
         const unsigned long long n = (unsigned long long)(step0 + s);
         field.inc();
@@ -102,7 +106,7 @@ __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, fl
         for (int k = 0; k < CPT; ++k) {
             if (!act[k]) continue;
             const int q = pidx[k];
-            hth[k] = thermal_field(p.seed, real[k], cell[k], n, p.sigma);
+            hth[k] = hpre[k];
             const float3 mi = xyz(M[q]);
             float3 nb = add3(xyz(M[q - 1]), xyz(M[q + 1]));
             nb = add3(nb, xyz(M[q - sy]));
@@ -128,6 +132,7 @@ __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, fl
             const float3 H = effective_field(nb, ti, hth[k], p.c_ex, p.c_an, Hn1);
             const float3 s1 = llg_torque(ti, H, p.alpha);
             M[q] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[k])));
+            hpre[k] = thermal_field(p.seed, real[k], cell[k], n + 1, p.sigma);
         }
         __syncthreads();
         Hn = Hn1;
@@ -658,17 +663,26 @@ bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_ki
     if (p.periodic != 0) return false;  // rods have free faces
     const size_t rod_pad = (size_t)(p.nx + 2) * (p.ny + 2) * (p.nz + 2);
     const size_t rod_bytes = rod_pad * 2 * sizeof(float4);
-    if (force_kind != 2 && rod_bytes <= (size_t)smem_optin && p.ncells <= 4 * kMaxThreads) {
-        plan->kind = 1;
+    const int rows = p.ny * p.nz;
+    const size_t PL = (size_t)(p.nz + 2) * p.ny;
+    const size_t pipe_bytes = ((size_t)p.nx + 2) * PL * sizeof(float4);
+    const bool twophase_fits = rod_bytes <= (size_t)smem_optin && p.ncells <= 4 * kMaxThreads;
+    const bool pipelined_fits = pipe_bytes <= (size_t)smem_optin && rows <= 4 * 672;
+    // Default (measured on GB300): rods of at most one CTA of threads use the two-phase kernel
+    // with one rod per CTA (many small CTAs per SM); larger rods use the plane-pipelined kernel.
+    int kind = force_kind;
+    if (kind == 0) kind = (p.ncells <= kMaxThreads && twophase_fits) ? 1 : (pipelined_fits ? 2 : 1);
+    if (kind == 1) {
+        if (!twophase_fits) return false;
         const int cpt = p.ncells <= kMaxThreads ? 1 : (p.ncells <= 2 * kMaxThreads ? 2 : 4);
         const int by_threads = std::max(1, kMaxThreads * cpt / p.ncells);
         const int by_smem = (int)std::max<size_t>(1, (size_t)smem_optin / rod_bytes);
-        const int by_spread = std::max(1, (n_real + nsm - 1) / nsm);
-        int rods = std::max(1, std::min({by_threads, by_smem, by_spread}));
+        int rods = 1;
         if (force_rods > 0) {
             if (force_rods > by_threads || force_rods > by_smem) return false;
             rods = force_rods;
         }
+        plan->kind = 1;
         plan->rods_per_cta = rods;
         plan->cells_per_thread = cpt;
         plan->threads = std::min(kMaxThreads, round_warp((rods * p.ncells + cpt - 1) / cpt));
@@ -677,11 +691,7 @@ bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_ki
         plan->ctas = (n_real + rods - 1) / rods;
         return true;
     }
-    if (force_kind == 1) return false;
-    const size_t PL = (size_t)(p.nz + 2) * p.ny;
-    const size_t bytes = ((size_t)p.nx + 2) * PL * sizeof(float4);
-    const int rows = p.ny * p.nz;
-    if (bytes > (size_t)smem_optin) return false;
+    if (!pipelined_fits) return false;
     int R = force_rows;
     if (R == 0) {
         // three rows per thread for the b = 1 rod's 1344 rows (448 threads, 128 registers):
@@ -694,7 +704,7 @@ bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_ki
     plan->threads = round_warp((rows + R - 1) / R);
     plan->rods_per_cta = 1;
     plan->cells_per_thread = 0;
-    plan->smem_bytes = bytes;
+    plan->smem_bytes = pipe_bytes;
     plan->ctas = n_real;
     return true;
 }

@@ -64,24 +64,34 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
     const int mplane = pitch * (G.TYmax + 4);
     float4 *Mb = sm4;                               // [3][mplane] state planes
     float4 *Tb = sm4 + 3 * mplane;                  // [2][mplane] predictor planes (same geometry)
+                                                    // then the staging table (int2 per position)
     const bool perx = p.periodic & 1u, pery = p.periodic & 2u;
     const size_t plane_cells = (size_t)G.NX * G.NY;
     const float4 *src = min + (size_t)real * plane_cells * G.NZ;
     float4 *dst = mout + (size_t)real * plane_cells * G.NZ;
     const PhiloxKeys keys = philox_keys(p.seed, p.real0 + (uint32_t)real);
 
-    // stage plane z (halo 2) into buffer b; out-of-domain positions are zero
+    // Staging table of this tile, built once: for every halo-2 position (smem offset in a plane,
+    // offset of its cell in a global plane or -1 outside a free face).  Each plane load is then a
+    // table read and a 16-byte asynchronous copy per position.
+    int2 *desc = reinterpret_cast<int2 *>(Tb + 2 * mplane);
+    const int w = TX + 4, h = TY + 4, npos = w * h;
+    for (int i = threadIdx.x; i < npos; i += blockDim.x) {
+        const int lx = i % w - 2, ly = i / w - 2;
+        int gx = x0 + lx, gy = y0 + ly;
+        const bool in = wrap(gx, G.NX, perx) && wrap(gy, G.NY, pery);
+        desc[i] = make_int2((ly + 2) * pitch + (lx + 2), in ? gy * G.NX + gx : -1);
+    }
+    __syncthreads();
     auto load_plane = [&](int z, int b) {
         float4 *dstp = Mb + b * mplane;
-        const int w = TX + 4, h = TY + 4;
-        for (int i = threadIdx.x; i < w * h; i += blockDim.x) {
-            const int lx = i % w - 2, ly = i / w - 2;
-            int gx = x0 + lx, gy = y0 + ly;
-            float4 *d = dstp + (ly + 2) * pitch + (lx + 2);
-            if (z < G.NZ && wrap(gx, G.NX, perx) && wrap(gy, G.NY, pery))
-                cp_async16(d, src + (size_t)z * plane_cells + (size_t)gy * G.NX + gx);
+        const float4 *srcp = src + (size_t)z * plane_cells;
+        for (int i = threadIdx.x; i < npos; i += blockDim.x) {
+            const int2 d = desc[i];
+            if (d.y >= 0)
+                cp_async16(dstp + d.x, srcp + d.y);
             else
-                *d = make_float4(0.f, 0.f, 0.f, 0.f);
+                dstp[d.x] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         cp_async_commit();
     };
@@ -128,7 +138,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
     float3 rA = zero3s(), rB = zero3s();
 
     load_plane(0, 0);
-    load_plane(1, 1);
+    if (G.NZ > 1) load_plane(1, 1);  // with one plane, plane 1 is never read (free z face)
     cp_async_wait_all();
     __syncthreads();
     // m(0) of the own columns
@@ -303,7 +313,9 @@ bool slab_plan(const KParams &p, int dev, SlabPlan *plan)
     int TYmax = (p.ny + tiles_y - 1) / tiles_y;
     // keep the columns per thread within the compiled variants and the shared memory within
     // the opt-in limit
-    auto smem_of = [&](int ty) { return (size_t)5 * (TXmax + 4) * (ty + 4) * sizeof(float4); };
+    auto smem_of = [&](int ty) {
+        return (size_t)5 * (TXmax + 4) * (ty + 4) * sizeof(float4) + (size_t)(TXmax + 4) * (ty + 4) * sizeof(int2);
+    };
     while (TYmax > 1 && (TXmax * TYmax > 4 * kSlabThreads || smem_of(TYmax) > (size_t)smem_optin)) {
         ++tiles_y;
         TYmax = (p.ny + tiles_y - 1) / tiles_y;
