@@ -59,6 +59,25 @@ def dist_env():
     return rank, world, local
 
 
+def realisation_offset(rank: int, n_real: int) -> int:
+    """First noise key of a rank's ensemble: ranks simulate disjoint realisations."""
+    return rank * n_real
+
+
+def weak_scaling_value(local_seconds: float, cell_steps_per_rank: float, device="cpu"):
+    """Whole-job throughput of a weak-scaling run: the cell-steps of all ranks divided by the
+    slowest rank's time (a max-reduction of the timings, the only collective; no data moves
+    between ranks).  Returns (value, max_seconds)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total = float(t.item())
+    return cell_steps_per_rank * world / total, total
+
+
 class Clocks:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -225,7 +244,7 @@ def run_ours(args):
     g = make_grid(pkg, cfg, pkg.ENGINE_RESIDENT)
     S_per_step = g.sample_every  # Heun steps per bench step (one sample)
     # each rank simulates its own 256 realisations (keys offset by rank): weak scaling
-    g.reset(seed=cfg["seed"], n_real=n_real, real_offset=rank * n_real)
+    g.reset(seed=cfg["seed"], n_real=n_real, real_offset=realisation_offset(rank, n_real))
     samples = torch.zeros((n_real, g.n_samples), device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, device="cuda")
 
@@ -241,15 +260,12 @@ def run_ours(args):
     clk = clocks.stop()
     g.sync(600)
     local_total = sum(times)
-    if world > 1:
-        t = torch.tensor([local_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
-        torch.distributed.barrier()
-    else:
-        total = local_total
     cells_per_step = n_real * ncell * S_per_step
-    value = cells_per_step * args.steps * world / total
+    value, total = weak_scaling_value(local_total, cells_per_step * args.steps,
+                                      device="cuda" if world > 1 else "cpu")
+    if world > 1:
+        torch.distributed.barrier()
+
     steps_per_loop = g.steps_per_loop
     loops_per_s = value / (ncell * steps_per_loop)
     launch_s = local_total / args.steps  # one persistent launch per step
@@ -280,8 +296,9 @@ def run_ours(args):
                        "l2": "flushed between steps (write of 2x L2)"},
             "loops_per_s": loops_per_s,
             "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
-                         "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": "rod_pipelined_kernel",
+                         "unit": "Gop/s", "frac": achieved / peak, "traffic": measured_traffic(),
+                         "traffic_unit": "bytes per launch (ncu dram read + write)",
+                         "kernel": "rod_pipelined_nx_kernel<3, 8, 24, 56>",
                          "ops_per_cell_step": ALU_OPS_PER_CELL_STEP,
                          "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x {MAX_SM_MHZ:.0f} MHz"},
             "clocks": clk,
@@ -358,6 +375,28 @@ def side_measurements(args, torch, pkg, cfg, g, samples, S_per_step, flush):
         "resident_loops_per_s": res["resident"] / (ncell1 * spl),
         "plain_loops_per_s": res["plain"] / (ncell1 * spl)}
     return out
+
+
+KERNEL_SOURCES = ("paper_1912_00310_gb300/csrc/k_rod.cu", "paper_1912_00310_gb300/csrc/physics.cuh",
+                  "paper_1912_00310_gb300/csrc/reduce.cuh")
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the resident kernel from the committed ncu capture, or None when
+    the kernel sources changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_rod_b1_256real.txt")
+    try:
+        kv = dict(line.split()[:2] for line in open(path) if line.strip() and not line.startswith("#"))
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest() == kv.get("kernel_sources_sha256"):
+            return float(kv["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
 
 
 def hbm_peak_gbs():
