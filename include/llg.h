@@ -111,11 +111,20 @@ llg_status llg_set_scaling(llg_ctx *ctx, int mode, double Tc_kelvin, double delt
  * A full loop is 2 |H_start - H_turn| / (rate dt) steps and 2 |H_start - H_turn| / sample_dH + 1
  * samples, sample k taken after step k * sample_every (sample 0 is the initial state).
  * rate = 0 (or H_start = H_turn) holds the field at H_start; sample_dH then counts steps.
- * shape: 0 = triangle (1 = the paper's sinusoid is not built: EUNSUPPORTED).
+ * shape: 0 = triangle; 1 = the paper's sinusoidal field H_max sin(2 pi f t) with H_max = H_start,
+ * SR = rate = 4 H_max f (the field-sweep paragraph), started at its maximum, i.e.
+ * H = H_max cos(2 pi n / period) with period = 4 H_max / (rate dt) steps (H_turn is ignored);
+ * sample_dH then sets the sample interval sample_dH / (rate dt) steps.
  * Errors: EINVAL (dt <= 0, rate < 0, the span or the sample spacing not a whole number of steps
- * to 1e-6 relative). */
+ * to 1e-6 relative; for the sinusoid, a period that is not an even whole number of steps and of
+ * sample intervals). */
 llg_status llg_set_sweep(llg_ctx *ctx, double H_start_Oe, double H_turn_Oe, double rate_Oe_per_ns,
                          double dt_s, double sample_dH_Oe, int shape);
+
+/* Cell volume (m^3) of the thermal field in place of (b a0)^3, for the paper's single-block
+ * limit: the whole rod as one rectangular-prism macrospin of volume 10752 a0^3 at b = 22 (the
+ * simulation-cell paragraph).  0 restores (b a0)^3.  Errors: EINVAL (negative). */
+llg_status llg_set_cell_volume(llg_ctx *ctx, double volume_m3);
 
 /* Select the integration engine (llg_engine).  Errors: EINVAL, EUNSUPPORTED (the engine cannot
  * hold this grid: checked at the next reset/advance). */

@@ -134,6 +134,8 @@ typedef struct {
     double H_start_Oe;   /* field at step 0                               */
     double H_turn_Oe;    /* field at the turning point                    */
     int64_t n_half;      /* steps from H_start to H_turn (0: constant)    */
+    int shape;           /* 0 triangle, 1 sinusoid of amplitude H_start   */
+    int64_t period;      /* sinusoid: steps per cycle, 1/(f dt)           */
 } orc_problem;
 
 typedef struct {
@@ -164,10 +166,17 @@ static orc_coeffs coeffs_of(const orc_problem *p)
     return r;
 }
 
-/* Zeeman field along z at step n, in Oe: a triangle wave from H_start to H_turn and back, with
- * n_half steps per half period. */
+/* Zeeman field along z at step n, in Oe.  shape 0: a triangle wave from H_start to H_turn and
+ * back, with n_half steps per half period.  shape 1: the sinusoidal field of the field-sweep
+ * paragraph, H_max sin(2 pi f t) with H_max = H_start and f = 1/(period dt), taken a quarter
+ * cycle on so that each loop starts at +H_max like the triangle; t is n dt reduced modulo the
+ * period. */
 double orc_field_Oe(const orc_problem *p, int64_t n)
 {
+    if (p->shape == 1) {
+        int64_t ph = n % p->period;
+        return p->H_start_Oe * sin(2.0 * ORC_PI * (double)ph / (double)p->period + 0.5 * ORC_PI);
+    }
     if (p->n_half <= 0) return p->H_start_Oe;
     int64_t period = 2 * p->n_half;
     int64_t ph = n % period;

@@ -43,7 +43,7 @@ class _Problem(C.Structure):
                 ("a", C.c_double), ("volume", C.c_double), ("A", C.c_double), ("K", C.c_double),
                 ("Ms", C.c_double), ("alpha", C.c_double), ("T", C.c_double), ("u", C.c_double * 3),
                 ("dt", C.c_double), ("H_start_Oe", C.c_double), ("H_turn_Oe", C.c_double),
-                ("n_half", C.c_int64)]
+                ("n_half", C.c_int64), ("shape", C.c_int), ("period", C.c_int64)]
 
 
 def lib():
@@ -148,6 +148,8 @@ class Problem:
     u: tuple = (0.0, 0.0, 1.0)
     periodic: int = 0
     volume: float | None = None
+    shape: int = 0     # 0 triangle, 1 sinusoid of amplitude H_start
+    period: int = 0    # sinusoid: steps per cycle
 
     @property
     def ncells(self) -> int:
@@ -163,23 +165,31 @@ class Problem:
             p.u[i] = self.u[i]
         p.dt = self.dt
         p.H_start_Oe, p.H_turn_Oe, p.n_half = self.H_start_Oe, self.H_turn_Oe, int(self.n_half)
+        p.shape, p.period = int(self.shape), int(self.period)
         return p
 
 
 def material_problem(nx, ny, nz, *, a0, b, A0, K0, Ms, alpha, T, dt, mode=1, Tc=858.0,
                      scale=(1.0, 1.0, 1.0), H_start_Oe=0.0, H_turn_Oe=0.0, rate_Oe_per_ns=0.0,
-                     periodic=0, u=(0.0, 0.0, 1.0)) -> Problem:
+                     periodic=0, u=(0.0, 0.0, 1.0), shape=0, volume=None) -> Problem:
     """Level-b problem from the unscaled material.  mode 0: A0, K0 unchanged (Fig. 2a);
     modes 1 and 2: A(b) = zeta A0 (Eq. 8), K(b) = zeta^3 K0 (Eq. 9).  scale = (s_K, s_alpha, s_Ms)
-    multiplies K(b), alpha and Ms.  The sweep is a triangle H_start -> H_turn -> H_start at the
-    given rate (Oe/ns)."""
+    multiplies K(b), alpha and Ms.  shape 0: the sweep is a triangle H_start -> H_turn -> H_start
+    at the given rate (Oe/ns).  shape 1: the sinusoid of amplitude H_max = H_start whose sweep
+    rate SR = 4 H_max f is the given rate, so a cycle is 4 H_max / (rate dt) steps.  volume
+    replaces (b a0)^3 in the thermal field (the single-block limit)."""
     z = zeta(b, T, Tc) if mode in (1, 2) else 1.0
     A = z * A0
     K = z ** 3 * K0 * scale[0]
-    n_half = sweep_steps(H_start_Oe, H_turn_Oe, rate_Oe_per_ns, dt)
+    period = 0
+    if shape == 1:
+        period = sweep_steps(4.0 * H_start_Oe, 0.0, rate_Oe_per_ns, dt)
+        n_half = period // 2
+    else:
+        n_half = sweep_steps(H_start_Oe, H_turn_Oe, rate_Oe_per_ns, dt)
     return Problem(nx, ny, nz, a=b * a0, A=A, K=K, Ms=Ms * scale[2], alpha=alpha * scale[1], T=T,
                    dt=dt, H_start_Oe=H_start_Oe, H_turn_Oe=H_turn_Oe, n_half=n_half, u=u,
-                   periodic=periodic)
+                   periodic=periodic, shape=shape, period=period, volume=volume)
 
 
 def sweep_steps(H_start_Oe, H_turn_Oe, rate_Oe_per_ns, dt) -> int:

@@ -91,6 +91,10 @@ class Grid:
         _lib.check(self._L.llg_set_sweep(self._h, H_start, H_turn, rate, dt, sample_dH, shape))
         return self
 
+    def set_cell_volume(self, volume_m3: float):
+        _lib.check(self._L.llg_set_cell_volume(self._h, volume_m3))
+        return self
+
     def set_engine(self, engine: int):
         _lib.check(self._L.llg_set_engine(self._h, engine))
         return self

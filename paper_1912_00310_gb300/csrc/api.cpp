@@ -23,6 +23,7 @@ struct llg_ctx {
     llg::MaterialIn mat{};
     llg::ScalingIn sc{1, 858.0, 0.511, 1.0, 1.0, 1.0};
     llg::SweepIn sw{};
+    double volume = 0.0;  // cell volume override (0: (b a0)^3)
     int engine = LLG_ENGINE_AUTO;
     int tune_kind = 0, tune_rods = 0, tune_rows = 0, tune_generic = 0, tune_balance = 1;
     long long chunk_steps = 1LL << 20;
@@ -85,7 +86,7 @@ llg_status derived_of(const llg_ctx *c, llg::Derived *d)
     if (!c->has_material) return fail(LLG_EINVAL, "material not set (llg_set_material)");
     if (!c->has_sweep) return fail(LLG_EINVAL, "sweep not set (llg_set_sweep)");
     char err[256];
-    if (!llg::derive(c->b, c->a0, c->mat, c->sc, c->sw, d, err, sizeof err)) return fail(LLG_EINVAL, "%s", err);
+    if (!llg::derive(c->b, c->a0, c->mat, c->sc, c->sw, d, err, sizeof err, c->volume)) return fail(LLG_EINVAL, "%s", err);
     return LLG_OK;
 }
 
@@ -288,19 +289,26 @@ llg_status llg_set_sweep(llg_ctx *c, double H_start_Oe, double H_turn_Oe, double
                          double sample_dH_Oe, int shape)
 {
     if (!c) return fail(LLG_EINVAL, "ctx is NULL");
-    if (shape == 1) return fail(LLG_EUNSUPPORTED, "the sinusoidal sweep is not built");
-    if (shape != 0) return fail(LLG_EINVAL, "shape must be 0 (triangle)");
+    if (shape != 0 && shape != 1) return fail(LLG_EINVAL, "shape must be 0 (triangle) or 1 (sinusoid)");
     if (!(dt_s > 0.0) || !(rate >= 0.0) || !(sample_dH_Oe > 0.0) || !std::isfinite(H_start_Oe) ||
         !std::isfinite(H_turn_Oe))
         return fail(LLG_EINVAL, "need dt > 0, rate >= 0, sample spacing > 0");
-    llg::SweepIn sw{H_start_Oe, H_turn_Oe, rate, dt_s, sample_dH_Oe};
+    llg::SweepIn sw{H_start_Oe, H_turn_Oe, rate, dt_s, sample_dH_Oe, shape};
     // validate now so that errors surface at the call that caused them
     const llg::MaterialIn mat = c->has_material ? c->mat : llg::MaterialIn{1e-11, 1e5, 0.0, 0.1, 0.0};
     llg::Derived d;
     char err[256];
-    if (!llg::derive(c->b, c->a0, mat, c->sc, sw, &d, err, sizeof err)) return fail(LLG_EINVAL, "%s", err);
+    if (!llg::derive(c->b, c->a0, mat, c->sc, sw, &d, err, sizeof err, c->volume)) return fail(LLG_EINVAL, "%s", err);
     c->sw = sw;
     c->has_sweep = true;
+    return LLG_OK;
+}
+
+llg_status llg_set_cell_volume(llg_ctx *c, double volume_m3)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (!(volume_m3 >= 0.0) || !std::isfinite(volume_m3)) return fail(LLG_EINVAL, "volume must be >= 0");
+    c->volume = volume_m3;
     return LLG_OK;
 }
 
@@ -602,14 +610,7 @@ llg_status llg_loop_area_grad(llg_ctx *c, int64_t n_steps, int objective, const 
         double sum = 0.0;
         for (int r = 0; r < c->n_real; ++r) sum += hs[(size_t)r * ns_total + (size_t)(k_first + k)];
         mbar[(size_t)k] = sum / c->n_real;
-        const long long n = (k_first + k) * se;
-        if (d.n_half > 0) {
-            const long long ph = n % (2 * d.n_half);
-            const long long tri = ph <= d.n_half ? ph : 2 * d.n_half - ph;
-            Hk[(size_t)k] = c->sw.H_start_Oe + (c->sw.H_turn_Oe - c->sw.H_start_Oe) * ((double)tri / (double)d.n_half);
-        } else {
-            Hk[(size_t)k] = c->sw.H_start_Oe;
-        }
+        Hk[(size_t)k] = llg::field_Oe(d, c->sw, (k_first + k) * se);
     }
     double L = 0.0;
     if (objective == 0) {
@@ -708,16 +709,7 @@ llg_status llg_sample_fields(const llg_ctx *c, double *H_Oe)
     llg::Derived d;
     llg_status s = derived_of(c, &d);
     if (s != LLG_OK) return s;
-    for (long long k = 0; k < d.n_samples; ++k) {
-        const long long n = k * d.sample_every;
-        if (d.n_half <= 0) {
-            H_Oe[k] = c->sw.H_start_Oe;
-            continue;
-        }
-        const long long ph = n % (2 * d.n_half);
-        const long long tri = ph <= d.n_half ? ph : 2 * d.n_half - ph;
-        H_Oe[k] = c->sw.H_start_Oe + (c->sw.H_turn_Oe - c->sw.H_start_Oe) * ((double)tri / (double)d.n_half);
-    }
+    for (long long k = 0; k < d.n_samples; ++k) H_Oe[k] = llg::field_Oe(d, c->sw, k * d.sample_every);
     return LLG_OK;
 }
 

@@ -89,8 +89,8 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
     __syncthreads();
 
     // ---- forward recomputation of the segment: seg[j] = state before step seg_start + j ----
-    Triangle field;
-    field.init(ap.seg_start, p.n_half, p.H0, p.slope);
+    Sweep field;
+    field.init(ap.seg_start, p);
     float Hn = field.value();
     for (int j = 0; j < ap.seg_len; ++j) {
         const unsigned long long n = (unsigned long long)(ap.seg_start + j);
@@ -129,11 +129,11 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
     const float a = -p.neg_dt_g1;  // dt g1
     const float ha = -p.neg_hdt_g1;
     const float alpha = p.alpha;
-    field.init(ap.seg_start + ap.seg_len - 1, p.n_half, p.H0, p.slope);
+    field.init(ap.seg_start + ap.seg_len - 1, p);
     for (int j = ap.seg_len - 1; j >= 0; --j) {
         const long long n = ap.seg_start + j;
         const float hn = field.value();
-        Triangle f1 = field;
+        Sweep f1 = field;
         f1.inc();
         const float hn1 = f1.value();
         // loss gradient of the state after step n, if it is a sample of the window
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
         }
         __syncthreads();
         // step back the field phase
-        if (p.n_half > 0) field.ph = (field.ph == 0 ? 2 * p.n_half : field.ph) - 1;
+        field.dec();
     }
     if (act) {
         lam[rod_off + 3 * c] = g.x;

@@ -4,8 +4,6 @@
 // resident engine is measured, and the engine for periodic grids that do not fit on chip.
 //
 // Layout: m, mt (predictor), acc (m + dt/2 f(m)), hth (thermal field) are [n_real][ncells][3].
-#include <cmath>
-
 #include "llg_internal.h"
 #include "physics.cuh"
 #include "reduce.cuh"
@@ -48,10 +46,18 @@ __device__ __forceinline__ float3 neighbour_sum(const float *s, int x, int y, in
     return add3(add3(add3(add3(add3(v[0], v[1]), v[2]), v[3]), v[4]), v[5]);
 }
 
+__device__ __forceinline__ float field_at(const KParams &p, unsigned long long n)
+{
+    Sweep sw;
+    sw.init((long long)n, p);
+    return sw.value();
+}
+
 __global__ void plain_pred_kernel(KParams p, const float *__restrict__ m, float *__restrict__ mt,
                                   float *__restrict__ acc, float *__restrict__ hth, int n_real,
-                                  unsigned long long n, float Hz)
+                                  unsigned long long n)
 {
+    const float Hz = field_at(p, n);
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (gid >= (long long)n_real * p.ncells) return;
     const int r = (int)(gid / p.ncells);
@@ -70,8 +76,9 @@ __global__ void plain_pred_kernel(KParams p, const float *__restrict__ m, float 
 
 __global__ void plain_corr_kernel(KParams p, float *__restrict__ m, const float *__restrict__ mt,
                                   const float *__restrict__ acc, const float *__restrict__ hth,
-                                  int n_real, float Hz1)
+                                  int n_real, unsigned long long n)
 {
+    const float Hz1 = field_at(p, n + 1);
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (gid >= (long long)n_real * p.ncells) return;
     const int r = (int)(gid / p.ncells);
@@ -110,29 +117,21 @@ constexpr int kThreads = 256;
 
 unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
-float host_field(const KParams &p, long long n)
-{
-    if (p.n_half <= 0) return p.H0;
-    const long long ph = n % (2 * p.n_half);
-    const long long tri = ph <= p.n_half ? ph : 2 * p.n_half - ph;
-    return std::fmaf(p.slope, (float)tri, p.H0);
-}
-
 }  // namespace
 
 cudaError_t plain_predictor(const KParams &p, const float *m, float *mt, float *acc, float *hth,
-                            int n_real, long long n, float Hz_n, cudaStream_t st)
+                            int n_real, long long n, cudaStream_t st)
 {
     plain_pred_kernel<<<blocks_for((long long)n_real * p.ncells), kThreads, 0, st>>>(
-        p, m, mt, acc, hth, n_real, (unsigned long long)n, Hz_n);
+        p, m, mt, acc, hth, n_real, (unsigned long long)n);
     return cudaGetLastError();
 }
 
 cudaError_t plain_corrector(const KParams &p, float *m, const float *mt, const float *acc,
-                            const float *hth, int n_real, float Hz_n1, cudaStream_t st)
+                            const float *hth, int n_real, long long n, cudaStream_t st)
 {
     plain_corr_kernel<<<blocks_for((long long)n_real * p.ncells), kThreads, 0, st>>>(
-        p, m, mt, acc, hth, n_real, Hz_n1);
+        p, m, mt, acc, hth, n_real, (unsigned long long)n);
     return cudaGetLastError();
 }
 
@@ -157,9 +156,9 @@ cudaError_t plain_advance(const KParams &p, float *m, float *mt, float *acc, flo
     long long count = 0;
     for (long long s = 0; s < n_steps; ++s) {
         const long long n = step0 + s;
-        cudaError_t e = plain_predictor(p, m, mt, acc, hth, n_real, n, host_field(p, n), st);
+        cudaError_t e = plain_predictor(p, m, mt, acc, hth, n_real, n, st);
         if (e != cudaSuccess) return e;
-        e = plain_corrector(p, m, mt, acc, hth, n_real, host_field(p, n + 1), st);
+        e = plain_corrector(p, m, mt, acc, hth, n_real, n, st);
         if (e != cudaSuccess) return e;
         count += 2;
         const long long done = n + 1;

@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, fl
     }
     __syncthreads();
 
-    Triangle field;
-    field.init(step0, p.n_half, p.H0, p.slope);
+    Sweep field;
+    field.init(step0, p);
     float Hn = field.value();
     const long long se = p.sample_every;
     long long next_sample = (samples && se > 0) ? (step0 / se + 1) * se : -1;
@@ -237,9 +237,9 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_ker
     bool pa = n_steps > 0, ca = false;
     long long sp = 0, sc = 0;
     int xp = 0, xc = 0;
-    Triangle fpred, fcorr;
-    fpred.init(step0, p.n_half, p.H0, p.slope);
-    fcorr.init(step0 + 1, p.n_half, p.H0, p.slope);
+    Sweep fpred, fcorr;
+    fpred.init(step0, p);
+    fcorr.init(step0 + 1, p);
     float Hp = fpred.value(), Hc = fcorr.value();
     const long long se = p.sample_every;
     long long next_sample = (samples && se > 0) ? (step0 / se + 1) * se : -1;
@@ -449,8 +449,8 @@ struct PipelinedRod {
         for (int j = 0; j < R; ++j) mA[j] = mB[j] = tA[j] = tB[j] = acc[j] = hth[j] = zero3();
         __syncthreads();
 
-        Triangle field;
-        field.init(s0, p.n_half, p.H0, p.slope);
+        Sweep field;
+        field.init(s0, p);
         float Hs = field.value();  // field at step s
         field.inc();
         float Hs1 = field.value();  // field at step s + 1

@@ -52,8 +52,7 @@ template <int CPT>
 __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, SlabGeom G,
                                                                     const float4 *__restrict__ min,
                                                                     float4 *__restrict__ mout,
-                                                                    unsigned long long n, float Hn,
-                                                                    float Hn1)
+                                                                    unsigned long long n)
 {
     extern __shared__ float4 sm4[];
     const int tx = blockIdx.x, ty = blockIdx.y, real = blockIdx.z;
@@ -70,6 +69,11 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
     const float4 *src = min + (size_t)real * plane_cells * G.NZ;
     float4 *dst = mout + (size_t)real * plane_cells * G.NZ;
     const PhiloxKeys keys = philox_keys(p.seed, p.real0 + (uint32_t)real);
+    Sweep sw;
+    sw.init((long long)n, p);
+    const float Hn = sw.value();
+    sw.inc();
+    const float Hn1 = sw.value();
 
     // Staging table of this tile, built once: for every halo-2 position (smem offset in a plane,
     // offset of its cell in a global plane or -1 outside a free face).  Each plane load is then a
@@ -290,14 +294,6 @@ __global__ void slab_sample_kernel(const float *__restrict__ partial, int nparts
     }
 }
 
-float host_field_at(const KParams &p, long long n)
-{
-    if (p.n_half <= 0) return p.H0;
-    const long long ph = n % (2 * p.n_half);
-    const long long tri = ph <= p.n_half ? ph : 2 * p.n_half - ph;
-    return std::fmaf(p.slope, (float)tri, p.H0);
-}
-
 }  // namespace
 
 bool slab_plan(const KParams &p, int dev, SlabPlan *plan)
@@ -354,11 +350,10 @@ cudaError_t slab_advance(const KParams &p, const SlabPlan &plan, float *m, int n
         e = cudaFuncSetAttribute(slab_step_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                  (int)plan.smem_bytes);                                               \
         if (e != cudaSuccess) return e;                                                               \
-        slab_step_kernel<C><<<grid, plan.threads, plan.smem_bytes, st>>>(p, G, a, b, n, Hn, Hn1);     \
+        slab_step_kernel<C><<<grid, plan.threads, plan.smem_bytes, st>>>(p, G, a, b, n);              \
         break;
     for (long long s = 0; s < n_steps; ++s) {
         const long long n = step0 + s;
-        const float Hn = host_field_at(p, n), Hn1 = host_field_at(p, n + 1);
         switch (plan.cols_per_thread) {
             LLG_SLAB(1)
             LLG_SLAB(2)

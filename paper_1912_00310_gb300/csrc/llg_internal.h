@@ -19,6 +19,8 @@ struct Derived {
     long long n_samples;                      // samples of one full loop
     long long steps_per_loop;
     double m_rescale;
+    int shape;                                // 0 triangle, 1 cosine
+    long long period;                         // steps per field cycle
 };
 
 // Per-job parameters handed to the kernels (FP32 coefficients).
@@ -31,6 +33,9 @@ struct KParams {
     float alpha;
     float H0, slope;          // triangle sweep, A/m and A/m per step
     long long n_half;
+    int shape;                // 0 triangle, 1 cosine
+    float amp;                // cosine amplitude, A/m
+    long long period;         // cosine period in steps
     uint32_t seed;
     uint32_t real0;           // key of realisation 0 of this ensemble
     long long sample_every;   // 0: no sampling
@@ -49,17 +54,23 @@ struct ScalingIn {
 };
 struct SweepIn {
     double H_start_Oe, H_turn_Oe, rate_Oe_per_ns, dt, sample_dH_Oe;
+    int shape;
 };
+// volume_m3 > 0 overrides the cell volume (b a0)^3 of the thermal field (a single block whose
+// volume is not a cube of the cell edge).
 bool derive(int b, double a0, const MaterialIn &m, const ScalingIn &s, const SweepIn &w, Derived *d,
-            char *err, size_t errlen);
+            char *err, size_t errlen, double volume_m3 = 0.0);
+// Field (Oe) at step n of a derived sweep (host, FP64).
+double field_Oe(const Derived &d, const SweepIn &w, long long n);
 KParams kparams_of(const Derived &d, int nx, int ny, int nz, unsigned periodic, double dt);
 
 // ---- plain engine (k_plain.cu): state in global memory, two launches per step --------------
 // m, mt: [n_real][ncells][3]; acc, hth: same shape (scratch).
+// The field of step n (predictor) and n + 1 (corrector) is evaluated on the device.
 cudaError_t plain_predictor(const KParams &p, const float *m, float *mt, float *acc, float *hth,
-                            int n_real, long long n, float Hz_n, cudaStream_t st);
+                            int n_real, long long n, cudaStream_t st);
 cudaError_t plain_corrector(const KParams &p, float *m, const float *mt, const float *acc,
-                            const float *hth, int n_real, float Hz_n1, cudaStream_t st);
+                            const float *hth, int n_real, long long n, cudaStream_t st);
 // samples[r][k] = mean over cells of m_z; sets *status = 1 on a non-finite mean.
 cudaError_t plain_sample(const KParams &p, const float *m, int n_real, long long k, float *samples,
                          int *status, cudaStream_t st);

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "llg_internal.h"
+
 namespace llg {
 
 // ------------------------------------------------------------------------------------------
@@ -148,27 +150,39 @@ __device__ __forceinline__ float3 effective_field(float3 nb, float3 m, float3 ht
                        fmaf(c_ex, nb.z, fmaf(c_an, m.z, hth.z + Hz)));
 }
 
-// Zeeman field along z of a triangle sweep, tracked by its phase in steps.
-struct Triangle {
-    long long ph;      // position in the period [0, 2 n_half)
-    long long n_half;  // 0: constant field
-    float H0, slope;   // A/m at phase 0; A/m per step of the triangle coordinate
+// Zeeman field along z at step n, tracked by its phase (n mod period) in steps:
+//   shape 0: triangle, H0 + slope * tri(ph) with tri = ph for ph <= n_half, period - ph after
+//            (period = 2 n_half; n_half = 0 holds H0);
+//   shape 1: cosine, amp * cos(2 pi ph / period) (the paper's sinusoidal field with its phase
+//            chosen to start at +amp).
+struct Sweep {
+    long long ph, period, n_half;
+    float H0, slope, amp;
+    int shape;
 
-    __device__ __forceinline__ void init(long long n, long long half, float h0, float sl)
+    __host__ __device__ __forceinline__ void init(long long n, const KParams &p)
     {
-        n_half = half;
-        H0 = h0;
-        slope = sl;
-        ph = half > 0 ? n % (2 * half) : 0;
+        shape = p.shape;
+        n_half = p.n_half;
+        period = p.shape == 1 ? p.period : 2 * p.n_half;
+        H0 = p.H0;
+        slope = p.slope;
+        amp = p.amp;
+        ph = period > 0 ? n % period : 0;
     }
     __device__ __forceinline__ float value() const
     {
+        if (shape == 1) return amp * cospif(2.0f * ((float)ph / (float)period));
         const long long tri = ph <= n_half ? ph : 2 * n_half - ph;
         return fmaf(slope, (float)tri, H0);
     }
-    __device__ __forceinline__ void inc()
+    __host__ __device__ __forceinline__ void inc()
     {
-        if (n_half > 0 && ++ph == 2 * n_half) ph = 0;
+        if (period > 0 && ++ph == period) ph = 0;
+    }
+    __host__ __device__ __forceinline__ void dec()
+    {
+        if (period > 0) ph = (ph == 0 ? period : ph) - 1;
     }
 };
 

@@ -31,7 +31,7 @@ double zeta_of(double b, double T, double Tc)
 }
 
 bool derive(int b, double a0, const MaterialIn &mat, const ScalingIn &sc, const SweepIn &sw,
-            Derived *d, char *err, size_t errlen)
+            Derived *d, char *err, size_t errlen, double volume_m3)
 {
     const bool cg = sc.mode == 1 || sc.mode == 2;
     d->zeta = cg ? zeta_of((double)b, mat.T, sc.Tc) : 1.0;
@@ -41,7 +41,7 @@ bool derive(int b, double a0, const MaterialIn &mat, const ScalingIn &sc, const 
     d->Ms = mat.Ms * sc.sMs;
     d->alpha = mat.alpha * sc.sAlpha;
     d->a = b * a0;
-    d->V = d->a * d->a * d->a;
+    d->V = volume_m3 > 0.0 ? volume_m3 : d->a * d->a * d->a;
     // Eq. 1 gyromagnetic factors
     d->g0 = kMu0 * kGammaE;
     d->g1 = d->g0 / (1.0 + d->alpha * d->alpha);
@@ -54,9 +54,33 @@ bool derive(int b, double a0, const MaterialIn &mat, const ScalingIn &sc, const 
     d->sigma = mat.T > 0.0
                    ? std::sqrt(2.0 * d->alpha * kBoltzmann * mat.T / (d->g0 * kMu0 * d->Ms * d->V * sw.dt))
                    : 0.0;
-    // triangle sweep
+    d->shape = sw.shape;
+    d->period = 0;
+    // sinusoidal sweep (the paper's H_max sin(2 pi f t), started at its maximum:
+    // H = H_max cos(2 pi n / period)), SR = 4 H_max f
     d->H_start_Am = sw.H_start_Oe * kAmPerOe;
     d->H_turn_Am = sw.H_turn_Oe * kAmPerOe;
+    if (sw.shape == 1) {
+        if (!(sw.H_start_Oe > 0.0) || !(sw.rate_Oe_per_ns > 0.0)) {
+            std::snprintf(err, errlen, "the sinusoidal sweep needs an amplitude H_start > 0 and a rate > 0");
+            return false;
+        }
+        const double per_step = sw.rate_Oe_per_ns * 1e9 * sw.dt;  // Oe of nominal sweep per step
+        d->period = whole_steps(4.0 * sw.H_start_Oe / per_step);
+        d->sample_every = whole_steps(sw.sample_dH_Oe / per_step);
+        if (d->period <= 0 || d->sample_every <= 0 || d->period % d->sample_every != 0 || d->period % 2 != 0) {
+            std::snprintf(err, errlen, "the period 4 H_max / (rate dt) must be an even whole number of steps "
+                                       "and a whole number of sample intervals");
+            return false;
+        }
+        d->n_half = d->period / 2;  // half a cycle: the descending branch
+        d->slope_Am = 0.0;
+        d->steps_per_loop = d->period;
+        d->n_samples = d->period / d->sample_every + 1;
+        d->m_rescale = sc.mode == 1 ? d->zeta : (sc.mode == 2 ? sc.delta * d->zeta + (1.0 - sc.delta) : 1.0);
+        return true;
+    }
+    // triangle sweep
     const double span = std::fabs(sw.H_start_Oe - sw.H_turn_Oe);
     if (sw.rate_Oe_per_ns > 0.0 && span > 0.0) {
         const double per_step = sw.rate_Oe_per_ns * 1e9 * sw.dt;  // Oe per step
@@ -110,10 +134,25 @@ KParams kparams_of(const Derived &d, int nx, int ny, int nz, unsigned periodic, 
     p.alpha = (float)d.alpha;
     p.H0 = (float)d.H_start_Am;
     p.slope = (float)d.slope_Am;
-    p.n_half = d.n_half;
+    p.n_half = d.shape == 1 ? 0 : d.n_half;
+    p.shape = d.shape;
+    p.amp = (float)d.H_start_Am;
+    p.period = d.period;
     p.sample_every = d.sample_every;
     p.n_samples = d.n_samples;
     return p;
+}
+
+double field_Oe(const Derived &d, const SweepIn &w, long long n)
+{
+    if (d.shape == 1) {
+        const long long ph = n % d.period;
+        return w.H_start_Oe * std::cos(2.0 * kPi * (double)ph / (double)d.period);
+    }
+    if (d.n_half <= 0) return w.H_start_Oe;
+    const long long ph = n % (2 * d.n_half);
+    const long long tri = ph <= d.n_half ? ph : 2 * d.n_half - ph;
+    return w.H_start_Oe + (w.H_turn_Oe - w.H_start_Oe) * ((double)tri / (double)d.n_half);
 }
 
 }  // namespace llg

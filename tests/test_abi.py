@@ -70,14 +70,39 @@ def test_coefficients_match_oracle(pkg, orc):
         g.close()
 
 
+def test_sinusoid_and_block_volume_match_oracle(pkg, orc):
+    from workloads import MAGNETITE as M, ROD_DIMS
+    b, dt = 4, 10e-15
+    g = _grid(pkg, b)
+    g.set_sweep(H_start=500.0, H_turn=0.0, rate=1000.0, dt=dt, sample_dH=1.0, shape=1)
+    p = orc.material_problem(*ROD_DIMS[b], a0=M["a0"], b=b, A0=M["A0"], K0=M["K0"], Ms=M["Ms"],
+                             alpha=M["alpha"], T=M["T"], dt=dt, H_start_Oe=500.0,
+                             rate_Oe_per_ns=1000.0, shape=1)
+    assert g.steps_per_loop == p.period == 200000
+    assert g.n_samples == 2001
+    H = g.sample_fields()
+    for k in (0, 1, 250, 500, 999, 1000, 1500, 2000):
+        assert H[k] == pytest.approx(orc.field_Oe(p, k * g.sample_every), abs=1e-9)
+    V = 10752 * M["a0"] ** 3
+    g.set_cell_volume(V)
+    q = orc.Problem(*ROD_DIMS[b], a=p.a, A=p.A, K=p.K, Ms=p.Ms, alpha=p.alpha, T=p.T, dt=dt, volume=V)
+    assert g.coefficients()["sigma"] == pytest.approx(orc.coefficients(q)["sigma"], rel=1e-12)
+    g.close()
+
+
 def test_sweep_validation(pkg):
     g = _grid(pkg)
     with pytest.raises(pkg.LLGError) as e:
         g.set_sweep(H_start=1500.0, H_turn=-1500.0, rate=1000.0, dt=10e-15, sample_dH=0.333)
     assert e.value.status == 1
+    with pytest.raises(pkg.LLGError) as e:  # a sinusoid period of 4 H_max / (rate dt) = 5 steps
+        g.set_sweep(H_start=1.25, H_turn=0.0, rate=1e5, dt=10e-15, sample_dH=1.0, shape=1)
+    assert e.value.status == 1
     with pytest.raises(pkg.LLGError) as e:
-        g.set_sweep(H_start=1500.0, H_turn=-1500.0, rate=1000.0, dt=10e-15, shape=1)
-    assert e.value.status == 6
+        g.set_sweep(H_start=1500.0, H_turn=-1500.0, rate=1000.0, dt=10e-15, shape=2)
+    assert e.value.status == 1
+    with pytest.raises(pkg.LLGError):
+        g.set_cell_volume(-1.0)
     with pytest.raises(pkg.LLGError):
         g.set_material(A0=1e-11, Ms=4.8e5, K0=1e4, alpha=0.1, T=310, u=(0.1, 0, 1))
     with pytest.raises(pkg.LLGError):

@@ -1,0 +1,189 @@
+"""GPU parity of the paper's own field protocol: the sinusoidal field H_max sin(2 pi f t) with
+SR = 4 H_max f (started at +H_max), and the single-block limit (the whole rod as one macrospin of
+volume 10752 a0^3 at b = 22, no exchange).
+
+Every engine evaluates the field from the same integer phase, so the engines stay bitwise equal;
+against the FP64 oracle the trajectories stay within 1e-4 over the first 1000 steps, past a
+wrap of the cycle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from workloads import MAGNETITE as M, ROD_DIMS, random_unit_state
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# A short cycle: 1 Oe per step at 10 fs, H_max = 200 Oe -> 800 steps per cycle, samples every 10.
+SINE = dict(H_start=200.0, rate=1e5, dt=10e-15, sample_dH=10.0)
+BLOCK_V = 10752 * M["a0"] ** 3
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1912_00310_gb300 import build
+    build.build()
+    import paper_1912_00310_gb300 as P
+    assert torch.cuda.is_available()
+    return P
+
+
+def sine_grid(pkg, dims, b, *, engine, kind=0, alpha=None, H_start=None, rate=None, dt=None,
+              sample_dH=None, volume=None, periodic=0):
+    g = pkg.Grid(*dims, a0=M["a0"], b=b, periodic=periodic)
+    g.set_material(A0=M["A0"], Ms=M["Ms"], K0=M["K0"], alpha=alpha or M["alpha"], T=M["T"])
+    g.set_scaling(mode=1, Tc=M["Tc"])
+    g.set_sweep(H_start=H_start or SINE["H_start"], H_turn=0.0, rate=rate or SINE["rate"],
+                dt=dt or SINE["dt"], sample_dH=sample_dH or SINE["sample_dH"], shape=1)
+    if volume:
+        g.set_cell_volume(volume)
+    g.set_engine(engine)
+    if kind:
+        g.set_tuning(pkg.TUNE_ROD_KIND, kind)
+    return g
+
+
+def sine_problem(orc, dims, b, *, alpha=None, H_start=None, rate=None, dt=None, volume=None,
+                 periodic=0):
+    return orc.material_problem(*dims, a0=M["a0"], b=b, A0=M["A0"], K0=M["K0"], Ms=M["Ms"],
+                                alpha=alpha or M["alpha"], T=M["T"], dt=dt or SINE["dt"], mode=1,
+                                Tc=M["Tc"], H_start_Oe=H_start or SINE["H_start"],
+                                rate_Oe_per_ns=rate or SINE["rate"], shape=1, volume=volume,
+                                periodic=periodic)
+
+
+def state_of(g, n_real):
+    out = torch.empty((n_real, g.ncells, 3), dtype=torch.float32, device="cuda")
+    g.get_state(out)
+    g.sync(300.0)
+    return out
+
+
+ENGINES = [("plain", 0), ("resident", 1), ("resident", 2), ("stream", 0)]
+
+
+def _engine(pkg, name):
+    return {"plain": pkg.ENGINE_PLAIN, "resident": pkg.ENGINE_RESIDENT,
+            "stream": pkg.ENGINE_STREAM}[name]
+
+
+def test_sinusoid_engines_bitwise_and_oracle(pkg, orc):
+    dims, b, n_real = ROD_DIMS[4], 4, 3
+    p = sine_problem(orc, dims, b)
+    assert p.period == 800
+    ref = orc.uniform_state(n_real, p.ncells)
+    orc.run(p, ref, seed=0, n_steps=1000)
+    states = []
+    for name, kind in ENGINES:
+        g = sine_grid(pkg, dims, b, engine=_engine(pkg, name), kind=kind)
+        assert g.steps_per_loop == 800 and g.n_samples == 81
+        g.reset(seed=0, n_real=n_real)
+        g.advance(600)
+        g.advance(400)  # crosses the end of the cycle at step 800
+        s = state_of(g, n_real)
+        assert float(np.max(np.abs(s.double().cpu().numpy() - ref))) <= 1e-4, (name, kind)
+        states.append(s)
+        g.close()
+    for s in states[1:]:
+        assert torch.equal(s, states[0])
+
+
+def test_sinusoid_samples_match_oracle(pkg, orc):
+    """A whole cycle on the b = 8 rod: every sample of m_z against the oracle."""
+    dims, b, n_real = ROD_DIMS[8], 8, 8
+    kw = dict(H_start=400.0, rate=1e5, dt=20e-15, sample_dH=40.0)  # 2 Oe/step, 800 steps
+    g = sine_grid(pkg, dims, b, engine=pkg.ENGINE_RESIDENT, **kw)
+    S = torch.zeros((n_real, g.n_samples), device="cuda")
+    g.run_loops(seed=0, n_real=n_real, samples=S, stats=False)
+    g.sync(60)
+    p = sine_problem(orc, dims, b, H_start=400.0, rate=1e5, dt=20e-15)
+    ref = orc.uniform_state(n_real, g.ncells)
+    s_ref, _ = orc.run(p, ref, seed=0, n_steps=g.steps_per_loop, sample_every=g.sample_every,
+                       n_samples=g.n_samples)
+    s_ref[:, 0] = 1.0
+    assert g.n_samples == 41 and g.sample_every == 20
+    assert np.max(np.abs(S.double().cpu().numpy() - s_ref)) < 1e-4
+    H = g.sample_fields()
+    for k in range(g.n_samples):
+        assert H[k] == pytest.approx(orc.field_Oe(p, k * g.sample_every), abs=1e-9)
+    g.close()
+
+
+def test_sinusoid_streaming_periodic_slab(pkg, orc):
+    """The streaming engine on a periodic slab several tiles wide, under the sinusoid."""
+    dims, n_real = (40, 45, 6), 1
+    g = sine_grid(pkg, dims, 1, engine=pkg.ENGINE_STREAM, dt=2e-15, rate=5e5, H_start=500.0,
+                  sample_dH=50.0, periodic=0b011)
+    h = sine_grid(pkg, dims, 1, engine=pkg.ENGINE_PLAIN, dt=2e-15, rate=5e5, H_start=500.0,
+                  sample_dH=50.0, periodic=0b011)
+    assert g.steps_per_loop == 2000
+    for x in (g, h):
+        x.reset(seed=3, n_real=n_real)
+        x.advance(300)
+    a, c = state_of(g, n_real), state_of(h, n_real)
+    assert torch.equal(a, c)
+    p = sine_problem(orc, dims, 1, H_start=500.0, rate=5e5, dt=2e-15, periodic=0b011)
+    ref = orc.uniform_state(n_real, p.ncells)
+    orc.run(p, ref, seed=3, n_steps=300)
+    assert float(np.max(np.abs(a.double().cpu().numpy() - ref))) <= 1e-4
+    g.close()
+    h.close()
+
+
+def test_sinusoid_adjoint_matches_oracle_gradient(pkg, orc):
+    dims, n_real, step0, n_steps = (1, 2, 3), 16, 130, 640  # the window holds the field's minimum
+    g = sine_grid(pkg, dims, 4, engine=pkg.ENGINE_RESIDENT)
+    g.reset(seed=0, n_real=n_real)
+    m0 = random_unit_state(n_real, 6, seed=5, cone=0.6).astype(np.float32)
+    g.set_state(m0, step0)
+    target = 0.5 * np.cos(2 * np.pi * np.arange(g.n_samples) / (g.n_samples - 1))
+    L, grad = g.loss_grad(n_steps, target, objective=0, ckpt_every=256)
+    p = sine_problem(orc, dims, 4)
+    Lo, go, _ = orc.loss_grad(p, m0.astype(np.float64), target=target, scale=(1.0, 1.0, 1.0),
+                              seed=0, step0=step0, n_steps=n_steps, sample_every=g.sample_every)
+    assert L == pytest.approx(Lo, rel=1e-3)
+    for k in range(3):
+        assert grad[k] == pytest.approx(go[k], rel=1e-2, abs=1e-3 * np.abs(go).max()), (k, grad, go)
+    g.close()
+
+
+def test_single_block_trajectory_and_loop(pkg, orc):
+    """b = 22: one prism of volume 10752 a0^3, 512 realisations.  Trajectories against the oracle
+    for 1000 steps, then a full +-500 Oe sinusoid at SR = 2500 Oe/ns: coercive field and area of
+    the GPU ensemble within 3 combined standard errors of the oracle's (same seeds)."""
+    dims, b, n_real, dt = (1, 1, 1), 22, 512, 20e-15
+    g = sine_grid(pkg, dims, b, engine=pkg.ENGINE_RESIDENT, H_start=500.0, rate=2500.0, dt=dt,
+                  sample_dH=5.0, volume=BLOCK_V)
+    p = sine_problem(orc, dims, b, H_start=500.0, rate=2500.0, dt=dt, volume=BLOCK_V)
+    assert g.steps_per_loop == p.period == 40000
+    c, oc = g.coefficients(), orc.coefficients(p)
+    assert c["sigma"] == pytest.approx(oc["sigma"], rel=1e-12)
+    g.reset(seed=11, n_real=n_real)
+    g.advance(1000)
+    gpu = state_of(g, n_real).double().cpu().numpy()
+    ref = orc.uniform_state(n_real, 1)
+    orc.run(p, ref, seed=11, n_steps=1000)
+    assert float(np.max(np.abs(gpu - ref))) <= 1e-4
+    g.close()
+
+    g = sine_grid(pkg, dims, b, engine=pkg.ENGINE_RESIDENT, H_start=500.0, rate=2500.0, dt=dt,
+                  sample_dH=5.0, volume=BLOCK_V)
+    S = np.zeros((n_real, g.n_samples), dtype=np.float32)
+    st = g.run_loops(seed=11, n_real=n_real, samples=S)
+    ref = orc.uniform_state(n_real, 1)
+    s_ref, _ = orc.run(p, ref, seed=11, n_steps=g.steps_per_loop, sample_every=g.sample_every,
+                       n_samples=g.n_samples)
+    s_ref[:, 0] = 1.0
+    H = g.sample_fields()
+    k_turn = (g.n_samples - 1) // 2
+    o = orc.loop_stats(H, s_ref, k_turn)
+    mine = orc.loop_stats(H, S.astype(np.float64), k_turn)
+    assert st["area_Oe"] == pytest.approx(mine["area"], rel=1e-6)
+    for key in ("Hc", "area"):
+        se = math.hypot(o[key + "_se"], mine[key + "_se"])
+        assert abs(o[key] - mine[key]) <= 3 * se, (key, o[key], mine[key], se)
+    assert 0 < mine["Hc"] < 500
+    g.close()

@@ -185,3 +185,39 @@ def test_triangle_sweep(orc):
     assert orc.field_Oe(p, 600000) == 1500.0
     assert orc.field_Oe(p, 600100) == pytest.approx(1499.0, abs=1e-9)
     assert orc.sample_interval(1.0, 1000.0, 1e-14) == 100
+
+
+def test_sinusoidal_sweep(orc):
+    """The paper's sinusoid H_max sin(2 pi f t) with SR = 4 H_max f: a cycle of 4 H_max / SR,
+    extremes +-H_max a half cycle apart, zeros at the quarter points, total variation 4 H_max
+    per cycle (so the mean |dH/dt| is SR) and peak slope 2 pi f H_max."""
+    dt, Hm, rate = 1e-14, 1500.0, 1000.0
+    p = orc.material_problem(1, 1, 1, a0=1e-9, b=1, A0=0.0, K0=0.0, Ms=1.0, alpha=0.1, T=0.0, dt=dt,
+                             mode=0, H_start_Oe=Hm, rate_Oe_per_ns=rate, shape=1)
+    P = p.period
+    assert P == 600000 and P * dt == pytest.approx(4 * Hm / (rate * 1e9), rel=1e-12)
+    H = np.array([orc.field_Oe(p, n) for n in range(0, P + 1, 100)])
+    assert H[0] == Hm and H[-1] == Hm
+    assert orc.field_Oe(p, P // 2) == pytest.approx(-Hm, abs=1e-9)
+    for q in (P // 4, 3 * P // 4):
+        assert orc.field_Oe(p, q) == pytest.approx(0.0, abs=1e-9)
+    assert orc.field_Oe(p, P // 8) == pytest.approx(Hm / math.sqrt(2.0), rel=1e-12)
+    assert np.sum(np.abs(np.diff(H))) == pytest.approx(4 * Hm, rel=1e-12)
+    f = 1.0 / (P * dt)
+    peak = max(abs(orc.field_Oe(p, n + 1) - orc.field_Oe(p, n)) for n in (P // 4, 3 * P // 4))
+    assert peak / dt == pytest.approx(2 * math.pi * f * Hm, rel=1e-6)
+    assert orc.field_Oe(p, 5 * P + 12345) == orc.field_Oe(p, 12345)
+    for n in (1, 777, 123456):
+        assert orc.field_Oe(p, P - n) == pytest.approx(orc.field_Oe(p, n), abs=1e-9)
+        assert orc.field_Oe(p, n + P // 2) == pytest.approx(-orc.field_Oe(p, n), abs=1e-9)
+
+
+def test_block_volume_is_a_cube_of_the_same_volume(orc):
+    """The thermal field depends on the cell only through its volume: a single block of volume
+    10752 a0^3 (the b = 22 prism) has the coefficients of a cube of edge (10752)^(1/3) a0."""
+    a0, V = 0.8396e-9, 10752 * 0.8396e-9 ** 3
+    kw = dict(A=0.0, K=1e4, Ms=480e3, alpha=0.1, T=310.0, dt=20e-15)
+    blk = orc.Problem(1, 1, 1, a=22 * a0, volume=V, **kw)
+    cube = orc.Problem(1, 1, 1, a=V ** (1.0 / 3.0), **kw)
+    assert orc.coefficients(blk)["sigma"] == pytest.approx(orc.coefficients(cube)["sigma"], rel=1e-14)
+    assert orc.coefficients(blk)["c_an"] == orc.coefficients(cube)["c_an"]
