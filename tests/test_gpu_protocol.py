@@ -152,13 +152,14 @@ def test_sinusoid_adjoint_matches_oracle_gradient(pkg, orc):
 
 def test_single_block_trajectory_and_loop(pkg, orc):
     """b = 22: one prism of volume 10752 a0^3, 512 realisations.  Trajectories against the oracle
-    for 1000 steps, then a full +-500 Oe sinusoid at SR = 2500 Oe/ns: coercive field and area of
-    the GPU ensemble within 3 combined standard errors of the oracle's (same seeds)."""
+    for 1000 steps, then a full +-400 Oe sinusoid at SR = 250 Oe/ns with alpha = 1 (at lower
+    damping or faster sweeps the macrospin does not reverse within the cycle): coercive field and
+    area of the GPU ensemble within 3 combined standard errors of the oracle's (same seeds)."""
     dims, b, n_real, dt = (1, 1, 1), 22, 512, 20e-15
-    g = sine_grid(pkg, dims, b, engine=pkg.ENGINE_RESIDENT, H_start=500.0, rate=2500.0, dt=dt,
-                  sample_dH=5.0, volume=BLOCK_V)
-    p = sine_problem(orc, dims, b, H_start=500.0, rate=2500.0, dt=dt, volume=BLOCK_V)
-    assert g.steps_per_loop == p.period == 40000
+    kw = dict(H_start=400.0, rate=250.0, dt=dt, alpha=1.0)
+    g = sine_grid(pkg, dims, b, engine=pkg.ENGINE_RESIDENT, sample_dH=4.0, volume=BLOCK_V, **kw)
+    p = sine_problem(orc, dims, b, volume=BLOCK_V, **kw)
+    assert g.steps_per_loop == p.period == 320000
     c, oc = g.coefficients(), orc.coefficients(p)
     assert c["sigma"] == pytest.approx(oc["sigma"], rel=1e-12)
     g.reset(seed=11, n_real=n_real)
@@ -169,8 +170,7 @@ def test_single_block_trajectory_and_loop(pkg, orc):
     assert float(np.max(np.abs(gpu - ref))) <= 1e-4
     g.close()
 
-    g = sine_grid(pkg, dims, b, engine=pkg.ENGINE_RESIDENT, H_start=500.0, rate=2500.0, dt=dt,
-                  sample_dH=5.0, volume=BLOCK_V)
+    g = sine_grid(pkg, dims, b, engine=pkg.ENGINE_RESIDENT, sample_dH=4.0, volume=BLOCK_V, **kw)
     S = np.zeros((n_real, g.n_samples), dtype=np.float32)
     st = g.run_loops(seed=11, n_real=n_real, samples=S)
     ref = orc.uniform_state(n_real, 1)
@@ -185,5 +185,5 @@ def test_single_block_trajectory_and_loop(pkg, orc):
     for key in ("Hc", "area"):
         se = math.hypot(o[key + "_se"], mine[key + "_se"])
         assert abs(o[key] - mine[key]) <= 3 * se, (key, o[key], mine[key], se)
-    assert 0 < mine["Hc"] < 500
+    assert 117 < mine["Hc"] < 400  # above the Stoner-Wohlfarth field 2K/(mu0 Ms), below H_max
     g.close()
