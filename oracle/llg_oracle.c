@@ -136,6 +136,8 @@ typedef struct {
     int64_t n_half;      /* steps from H_start to H_turn (0: constant)    */
     int shape;           /* 0 triangle, 1 sinusoid of amplitude H_start   */
     int64_t period;      /* sinusoid: steps per cycle, 1/(f dt)           */
+    double disp;         /* easy-axis dispersion: half-angle (rad) of the cone about z in which
+                            each cell's axis lies (0: every cell has the axis u) */
 } orc_problem;
 
 typedef struct {
@@ -186,10 +188,44 @@ double orc_field_Oe(const orc_problem *p, int64_t n)
 
 static int64_t ncells_of(const orc_problem *p) { return (int64_t)p->nx * p->ny * p->nz; }
 
+/* Easy axis of one cell of one realisation.  With disp = 0 it is the material axis u.  With
+ * disp > 0 it models the lattice disorder of the material paragraph (a 5 degree dispersion of
+ * the anisotropy axis): a direction uniform over the solid angle of the cone of half-angle disp
+ * about z, drawn once per (seed, realisation, cell) from Philox4x32-10 with counter
+ * (cell, 0, 0, 1) (the thermal draws use the tag word 0): for a uniform point of a spherical cap,
+ * 1 - cos(theta) is uniform on [0, 1 - cos(disp)] and the azimuth is uniform. */
+void orc_easy_axis(const orc_problem *p, uint32_t seed, uint32_t real, uint32_t cell, double u[3])
+{
+    if (!(p->disp > 0.0)) {
+        u[0] = p->u[0];
+        u[1] = p->u[1];
+        u[2] = p->u[2];
+        return;
+    }
+    uint32_t ctr[4] = {cell, 0u, 0u, 1u};
+    uint32_t key[2] = {seed, real};
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, key, x);
+    const double one_minus_cos = orc_uniform24(x[0]) * (1.0 - cos(p->disp));
+    const double phi = 2.0 * ORC_PI * orc_uniform24(x[1]);
+    const double cos_t = 1.0 - one_minus_cos;
+    const double sin_t = sqrt(one_minus_cos * (2.0 - one_minus_cos));
+    u[0] = sin_t * cos(phi);
+    u[1] = sin_t * sin(phi);
+    u[2] = cos_t;
+}
+
+/* Axes of all cells of one realisation, [N][3]. */
+static void easy_axes(const orc_problem *p, uint32_t seed, uint32_t real, double *ax)
+{
+    const int64_t N = ncells_of(p);
+    for (int64_t i = 0; i < N; ++i) orc_easy_axis(p, seed, real, (uint32_t)i, ax + 3 * i);
+}
+
 /* Effective field at cell (x,y,z) of state m (unit vectors), field Hz (A/m) along z, thermal
- * field hth. */
+ * field hth, easy axes ax [N][3]. */
 static void effective_field(const orc_problem *p, const orc_coeffs *c, const double *m, int x, int y,
-                            int z, double Hz, const double *hth, double H[3])
+                            int z, double Hz, const double *hth, const double *ax, double H[3])
 {
     double s[3] = {0.0, 0.0, 0.0};
     const int dims[3] = {p->nx, p->ny, p->nz};
@@ -209,9 +245,9 @@ static void effective_field(const orc_problem *p, const orc_coeffs *c, const dou
         }
     }
     int64_t i = x + (int64_t)p->nx * (y + (int64_t)p->ny * z);
-    const double *mi = m + 3 * i;
-    double mu = mi[0] * p->u[0] + mi[1] * p->u[1] + mi[2] * p->u[2];
-    for (int k = 0; k < 3; ++k) H[k] = c->c_ex * s[k] + c->c_an * mu * p->u[k] + hth[k];
+    const double *mi = m + 3 * i, *u = ax + 3 * i;
+    double mu = mi[0] * u[0] + mi[1] * u[1] + mi[2] * u[2];
+    for (int k = 0; k < 3; ++k) H[k] = c->c_ex * s[k] + c->c_an * mu * u[k] + hth[k];
     H[2] += Hz;
 }
 
@@ -234,6 +270,7 @@ static void normalise(double v[3])
 
 typedef struct {
     double *mt, *f0, *hth;
+    double *ax;  /* easy axes of the realisation being stepped */
 } work_buffers;
 
 /* One Heun step n -> n+1 of one realisation, in place on m. */
@@ -259,7 +296,7 @@ static void heun_step(const orc_problem *p, const orc_coeffs *c, uint32_t seed, 
             for (int x = 0; x < p->nx; ++x) {
                 int64_t i = x + (int64_t)p->nx * (y + (int64_t)p->ny * z);
                 double H[3];
-                effective_field(p, c, m, x, y, z, Hn, w->hth + 3 * i, H);
+                effective_field(p, c, m, x, y, z, Hn, w->hth + 3 * i, w->ax, H);
                 llg_rhs(c, m + 3 * i, H, w->f0 + 3 * i);
                 for (int k = 0; k < 3; ++k) w->mt[3 * i + k] = m[3 * i + k] + p->dt * w->f0[3 * i + k];
                 normalise(w->mt + 3 * i);
@@ -270,7 +307,7 @@ static void heun_step(const orc_problem *p, const orc_coeffs *c, uint32_t seed, 
             for (int x = 0; x < p->nx; ++x) {
                 int64_t i = x + (int64_t)p->nx * (y + (int64_t)p->ny * z);
                 double H[3], f1[3];
-                effective_field(p, c, w->mt, x, y, z, Hn1, w->hth + 3 * i, H);
+                effective_field(p, c, w->mt, x, y, z, Hn1, w->hth + 3 * i, w->ax, H);
                 llg_rhs(c, w->mt + 3 * i, H, f1);
                 for (int k = 0; k < 3; ++k)
                     m[3 * i + k] = m[3 * i + k] + 0.5 * p->dt * (w->f0[3 * i + k] + f1[k]);
@@ -314,6 +351,8 @@ static void run_one(run_job *job, int r)
     w.mt = (double *)malloc(sizeof(double) * 3 * N);
     w.f0 = (double *)malloc(sizeof(double) * 3 * N);
     w.hth = (double *)malloc(sizeof(double) * 3 * N);
+    w.ax = (double *)malloc(sizeof(double) * 3 * N);
+    easy_axes(p, job->seed, job->real0 + (uint32_t)r, w.ax);
     double *m = job->m_state + (int64_t)r * N * 3;
     double acc = 0.0;
     int64_t acc_n = 0;
@@ -334,6 +373,7 @@ static void run_one(run_job *job, int r)
     free(w.mt);
     free(w.f0);
     free(w.hth);
+    free(w.ax);
 }
 
 static void *run_worker(void *arg)
@@ -384,8 +424,9 @@ int orc_run(const orc_problem *p, uint32_t seed, int n_real, uint32_t real0, int
 }
 
 /* Total energy (J) of a state at field H (Oe along z): exchange per nearest-neighbour pair
- * 2 A a (1 - m_i . m_j), anisotropy -K V (m.u)^2, Zeeman -mu0 Ms V H m_z.  The effective field of
- * Eq. 1 is -(1/(mu0 Ms V)) dE/dm_i of this energy. */
+ * 2 A a (1 - m_i . m_j), anisotropy -K V (m.u)^2 with the material axis u (no dispersion),
+ * Zeeman -mu0 Ms V H m_z.  The effective field of Eq. 1 is -(1/(mu0 Ms V)) dE/dm_i of this
+ * energy. */
 double orc_energy(const orc_problem *p, const double *m, double H_Oe)
 {
     const double H = H_Oe * ORC_OE_TO_AM;
@@ -619,7 +660,7 @@ static dcoeffs dual_coefficients(const orc_problem *p, const double scale[3])
 }
 
 static dvec dual_field(const orc_problem *p, const dcoeffs *c, const dvec *m, int x, int y, int z,
-                       double Hz, dvec hth)
+                       double Hz, dvec hth, const double *ax)
 {
     dvec s = {dconst(0.0), dconst(0.0), dconst(0.0)};
     const int dims[3] = {p->nx, p->ny, p->nz};
@@ -637,9 +678,14 @@ static dvec dual_field(const orc_problem *p, const dcoeffs *c, const dvec *m, in
         }
     }
     int64_t i = x + (int64_t)p->nx * (y + (int64_t)p->ny * z);
-    /* easy axis along z: anisotropy field c_an m_z z */
+    /* anisotropy field c_an (m.u) u of the cell's easy axis u */
+    const double *u = ax + 3 * i;
+    dual mu = dadd(dadd(dscale(u[0], m[i].x), dscale(u[1], m[i].y)), dscale(u[2], m[i].z));
+    dual a = dmul(c->c_an, mu);
     dvec H = dv_add(dv_scale(c->c_ex, s), hth);
-    H.z = dadd(H.z, dadd(dmul(c->c_an, m[i].z), dconst(Hz)));
+    H.x = dadd(H.x, dscale(u[0], a));
+    H.y = dadd(H.y, dscale(u[1], a));
+    H.z = dadd(H.z, dadd(dscale(u[2], a), dconst(Hz)));
     return H;
 }
 
@@ -675,12 +721,14 @@ static void *grad_worker(void *arg)
     dvec *mt = (dvec *)malloc(sizeof(dvec) * (size_t)N);
     dvec *f0 = (dvec *)malloc(sizeof(dvec) * (size_t)N);
     dvec *hth = (dvec *)malloc(sizeof(dvec) * (size_t)N);
+    double *ax = (double *)malloc(sizeof(double) * 3 * (size_t)N);
     dual *local = (dual *)calloc((size_t)J->n_k, sizeof(dual));
     for (;;) {
         pthread_mutex_lock(&J->lock);
         int r = J->next_real++;
         pthread_mutex_unlock(&J->lock);
         if (r >= J->n_real) break;
+        easy_axes(p, J->seed, J->real0 + (uint32_t)r, ax);
         for (int64_t i = 0; i < N; ++i) {
             const double *mi = J->m0 + ((int64_t)r * N + i) * 3;
             m[i].x = dconst(mi[0]);
@@ -701,7 +749,7 @@ static void *grad_worker(void *arg)
                 for (int y = 0; y < p->ny; ++y)
                     for (int x = 0; x < p->nx; ++x) {
                         int64_t i = x + (int64_t)p->nx * (y + (int64_t)p->ny * z);
-                        dvec H = dual_field(p, &c, m, x, y, z, Hn, hth[i]);
+                        dvec H = dual_field(p, &c, m, x, y, z, Hn, hth[i], ax);
                         f0[i] = dual_rhs(&c, m[i], H);
                         mt[i] = dv_normalise(dv_add(m[i], dv_scale(dconst(dt), f0[i])));
                     }
@@ -709,7 +757,7 @@ static void *grad_worker(void *arg)
                 for (int y = 0; y < p->ny; ++y)
                     for (int x = 0; x < p->nx; ++x) {
                         int64_t i = x + (int64_t)p->nx * (y + (int64_t)p->ny * z);
-                        dvec H = dual_field(p, &c, mt, x, y, z, Hn1, hth[i]);
+                        dvec H = dual_field(p, &c, mt, x, y, z, Hn1, hth[i], ax);
                         dvec f1 = dual_rhs(&c, mt[i], H);
                         m[i] = dv_normalise(dv_add(m[i], dv_scale(dconst(0.5 * dt), dv_add(f0[i], f1))));
                     }
@@ -731,6 +779,7 @@ static void *grad_worker(void *arg)
     free(mt);
     free(f0);
     free(hth);
+    free(ax);
     free(local);
     return NULL;
 }

@@ -43,7 +43,8 @@ class _Problem(C.Structure):
                 ("a", C.c_double), ("volume", C.c_double), ("A", C.c_double), ("K", C.c_double),
                 ("Ms", C.c_double), ("alpha", C.c_double), ("T", C.c_double), ("u", C.c_double * 3),
                 ("dt", C.c_double), ("H_start_Oe", C.c_double), ("H_turn_Oe", C.c_double),
-                ("n_half", C.c_int64), ("shape", C.c_int), ("period", C.c_int64)]
+                ("n_half", C.c_int64), ("shape", C.c_int), ("period", C.c_int64),
+                ("disp", C.c_double)]
 
 
 def lib():
@@ -59,6 +60,7 @@ def lib():
             L.orc_thermal_normals.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64, dp]
             L.orc_zeta.argtypes = [C.c_double] * 3
             L.orc_zeta.restype = C.c_double
+            L.orc_easy_axis.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, dp]
             L.orc_exchange_length.argtypes = [C.c_double] * 3
             L.orc_exchange_length.restype = C.c_double
             L.orc_m_rescale.argtypes = [C.c_int, C.c_double, C.c_double]
@@ -116,6 +118,18 @@ def thermal_normals(seed: int, real: int, cell: int, step: int) -> np.ndarray:
     return out
 
 
+def easy_axes(p: Problem, seed: int, n_real: int, real0: int = 0) -> np.ndarray:
+    """Easy axis of every cell of every realisation, [n_real][ncells][3]."""
+    pc = p._c()
+    out = np.zeros((n_real, p.ncells, 3))
+    L = lib()
+    for r in range(n_real):
+        for i in range(p.ncells):
+            L.orc_easy_axis(C.byref(pc), seed & 0xFFFFFFFF, (real0 + r) & 0xFFFFFFFF, i,
+                            _dp(out[r, i]))
+    return out
+
+
 def zeta(b: float, T: float, Tc: float) -> float:
     """Eq. 11's coarse-graining factor zeta(b) = t/b + 1 - t, t = T/Tc."""
     return lib().orc_zeta(b, T, Tc)
@@ -150,6 +164,7 @@ class Problem:
     volume: float | None = None
     shape: int = 0     # 0 triangle, 1 sinusoid of amplitude H_start
     period: int = 0    # sinusoid: steps per cycle
+    disp: float = 0.0  # easy-axis dispersion: cone half-angle about z (rad), 0 = the axis u
 
     @property
     def ncells(self) -> int:
@@ -166,18 +181,20 @@ class Problem:
         p.dt = self.dt
         p.H_start_Oe, p.H_turn_Oe, p.n_half = self.H_start_Oe, self.H_turn_Oe, int(self.n_half)
         p.shape, p.period = int(self.shape), int(self.period)
+        p.disp = float(self.disp)
         return p
 
 
 def material_problem(nx, ny, nz, *, a0, b, A0, K0, Ms, alpha, T, dt, mode=1, Tc=858.0,
                      scale=(1.0, 1.0, 1.0), H_start_Oe=0.0, H_turn_Oe=0.0, rate_Oe_per_ns=0.0,
-                     periodic=0, u=(0.0, 0.0, 1.0), shape=0, volume=None) -> Problem:
+                     periodic=0, u=(0.0, 0.0, 1.0), shape=0, volume=None, disp=0.0) -> Problem:
     """Level-b problem from the unscaled material.  mode 0: A0, K0 unchanged (Fig. 2a);
     modes 1 and 2: A(b) = zeta A0 (Eq. 8), K(b) = zeta^3 K0 (Eq. 9).  scale = (s_K, s_alpha, s_Ms)
     multiplies K(b), alpha and Ms.  shape 0: the sweep is a triangle H_start -> H_turn -> H_start
     at the given rate (Oe/ns).  shape 1: the sinusoid of amplitude H_max = H_start whose sweep
     rate SR = 4 H_max f is the given rate, so a cycle is 4 H_max / (rate dt) steps.  volume
-    replaces (b a0)^3 in the thermal field (the single-block limit)."""
+    replaces (b a0)^3 in the thermal field (the single-block limit).  disp (rad) spreads each
+    cell's easy axis uniformly over the cone of that half-angle about z."""
     z = zeta(b, T, Tc) if mode in (1, 2) else 1.0
     A = z * A0
     K = z ** 3 * K0 * scale[0]
@@ -189,7 +206,7 @@ def material_problem(nx, ny, nz, *, a0, b, A0, K0, Ms, alpha, T, dt, mode=1, Tc=
         n_half = sweep_steps(H_start_Oe, H_turn_Oe, rate_Oe_per_ns, dt)
     return Problem(nx, ny, nz, a=b * a0, A=A, K=K, Ms=Ms * scale[2], alpha=alpha * scale[1], T=T,
                    dt=dt, H_start_Oe=H_start_Oe, H_turn_Oe=H_turn_Oe, n_half=n_half, u=u,
-                   periodic=periodic, shape=shape, period=period, volume=volume)
+                   periodic=periodic, shape=shape, period=period, volume=volume, disp=disp)
 
 
 def sweep_steps(H_start_Oe, H_turn_Oe, rate_Oe_per_ns, dt) -> int:
