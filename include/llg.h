@@ -93,8 +93,9 @@ llg_status llg_set_stream(llg_ctx *ctx, void *cuda_stream);
 /* Material parameters of the unscaled (b = 1) system, material paragraph and Eq. 1:
  * A0 exchange stiffness (J/m), Ms saturation magnetisation (A/m), K0 uniaxial anisotropy
  * (J/m^3) along the unit vector u, alpha Gilbert damping, T temperature (K).  The engines of this
- * build support u = +z or -z only (EUNSUPPORTED otherwise); the paper's 5-degree axis
- * dispersion is not modelled.  Errors: EINVAL (Ms <= 0, alpha < 0, T < 0, A0 < 0, |u| = 0). */
+ * build support u = +z or -z only (EUNSUPPORTED otherwise); the paper's 5-degree dispersion of
+ * the axis is set by llg_set_axis_dispersion.  Errors: EINVAL (Ms <= 0, alpha < 0, T < 0, A0 < 0,
+ * |u| = 0). */
 llg_status llg_set_material(llg_ctx *ctx, double A0, double Ms, double K0, const double u[3],
                             double alpha, double T_kelvin);
 
@@ -125,6 +126,23 @@ llg_status llg_set_sweep(llg_ctx *ctx, double H_start_Oe, double H_turn_Oe, doub
  * limit: the whole rod as one rectangular-prism macrospin of volume 10752 a0^3 at b = 22 (the
  * simulation-cell paragraph).  0 restores (b a0)^3.  Errors: EINVAL (negative). */
 llg_status llg_set_cell_volume(llg_ctx *ctx, double volume_m3);
+
+/* Easy-axis dispersion (the material paragraph's 5-degree spread of the anisotropy axis, modelling
+ * lattice disorder): with half_angle_rad > 0 every cell of every realisation gets its own easy
+ * axis, uniform over the solid angle of the cone of that half-angle about z, drawn from
+ * Philox4x32-10 with key (seed, realisation) and counter (cell, 0, 0, 1), so it is fixed by the
+ * ensemble's seed and realisation numbers like the thermal field (the thermal draws use counter
+ * word 3 = 0).  The anisotropy field of a cell is then c_an (m.u) u.  The axes are drawn on the
+ * context's stream at the next launch after a reset and kept in device memory (16 bytes per
+ * cell and realisation).  0 (the default) restores the axis z everywhere.  Every engine, the
+ * batching layer and llg_loop_area_grad honour it; llg_plain_advance_noalloc rejects it
+ * (EUNSUPPORTED).  Errors: EINVAL (outside [0, pi/2]). */
+llg_status llg_set_axis_dispersion(llg_ctx *ctx, double half_angle_rad);
+
+/* The easy axes of the current ensemble, u [n_real][ncells][3] (x, y, z; host or device memory,
+ * caller-owned; the z axis in every cell when no dispersion is set).  A host copy is complete on
+ * return; a device copy is ordered on the context's stream.  Errors: EINVAL (no ensemble). */
+llg_status llg_get_axes(llg_ctx *ctx, float *u);
 
 /* Select the integration engine (llg_engine).  Errors: EINVAL, EUNSUPPORTED (the engine cannot
  * hold this grid: checked at the next reset/advance). */

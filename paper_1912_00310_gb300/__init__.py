@@ -91,6 +91,16 @@ class Grid:
         _lib.check(self._L.llg_set_sweep(self._h, H_start, H_turn, rate, dt, sample_dH, shape))
         return self
 
+    def set_axis_dispersion(self, half_angle_rad: float):
+        """Per-cell easy axes uniform over the cone of this half-angle about z (0: axis z)."""
+        _lib.check(self._L.llg_set_axis_dispersion(self._h, half_angle_rad))
+        return self
+
+    def get_axes(self, out):
+        """Copy the ensemble's easy axes [n_real][ncells][3] into out (host or device)."""
+        _lib.check(self._L.llg_get_axes(self._h, C.c_void_p(_ptr(out))))
+        return out
+
     def set_cell_volume(self, volume_m3: float):
         _lib.check(self._L.llg_set_cell_volume(self._h, volume_m3))
         return self

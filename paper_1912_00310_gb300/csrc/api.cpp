@@ -24,6 +24,13 @@ struct llg_ctx {
     llg::ScalingIn sc{1, 858.0, 0.511, 1.0, 1.0, 1.0};
     llg::SweepIn sw{};
     double volume = 0.0;  // cell volume override (0: (b a0)^3)
+    double disp = 0.0;    // easy-axis dispersion: cone half-angle (rad) about z, 0 = axis z
+    float4 *d_axis = nullptr;  // [n_real][ncells] easy axes when disp > 0
+    size_t axis_cap = 0;       // float4 entries
+    bool axis_ok = false;      // d_axis holds the axes of (ax_seed, ax_real0, ax_n, ax_disp)
+    uint32_t ax_seed = 0, ax_real0 = 0;
+    int ax_n = 0;
+    double ax_disp = 0.0;
     int engine = LLG_ENGINE_AUTO;
     int tune_kind = 0, tune_rods = 0, tune_rows = 0, tune_generic = 0, tune_balance = 1;
     long long chunk_steps = 1LL << 20;
@@ -107,6 +114,43 @@ llg_status grow(float **buf, size_t *cap, size_t need_floats)
     return LLG_OK;
 }
 
+// The easy axes of the ensemble in the dispersed-axis mode, drawn on the context's stream when
+// the ensemble's keys or the dispersion changed; *out = NULL in the z-axis mode.
+llg_status ensure_axes(llg_ctx *c, const float4 **out)
+{
+    *out = nullptr;
+    if (!(c->disp > 0.0)) return LLG_OK;
+    if (c->n_real < 1) return fail(LLG_EINVAL, "no ensemble (llg_reset first)");
+    if (c->axis_ok && c->ax_seed == c->seed && c->ax_real0 == c->real0 && c->ax_n == c->n_real &&
+        c->ax_disp == c->disp) {
+        *out = c->d_axis;
+        return LLG_OK;
+    }
+    const size_t need = (size_t)c->n_real * (size_t)ncells_of(c);
+    if (c->axis_cap < need) {
+        cudaFree(c->d_axis);
+        c->d_axis = nullptr;
+        c->axis_cap = 0;
+        cudaError_t e = cudaMalloc(&c->d_axis, need * sizeof(float4));
+        if (e != cudaSuccess) {
+            c->d_axis = nullptr;
+            cudaGetLastError();
+            return fail(LLG_ENOMEM, "cudaMalloc of %zu bytes (easy axes) failed", need * sizeof(float4));
+        }
+        c->axis_cap = need;
+    }
+    const float w_max = (float)(1.0 - std::cos(c->disp));
+    LLG_CUDA(llg::axis_fill(c->d_axis, c->n_real, (int)ncells_of(c), c->seed, c->real0, w_max, c->stream),
+             "easy-axis draw");
+    c->axis_ok = true;
+    c->ax_seed = c->seed;
+    c->ax_real0 = c->real0;
+    c->ax_n = c->n_real;
+    c->ax_disp = c->disp;
+    *out = c->d_axis;
+    return LLG_OK;
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev)
@@ -171,6 +215,11 @@ llg_status ctx_view(llg_ctx *c, CtxView *v)
     v->kp = kparams_of(d, c->nx, c->ny, c->nz, c->periodic, c->sw.dt);
     v->kp.seed = c->seed;
     v->kp.real0 = c->real0;
+    if (c->n_real > 0) {
+        DeviceGuard g(c->device);
+        const llg_status sa = ensure_axes(c, &v->kp.axis);
+        if (sa != LLG_OK) return sa;
+    }
     v->tune_kind = c->tune_kind;
     v->tune_rods = c->tune_rods;
     v->tune_rows = c->tune_rows;
@@ -185,6 +234,7 @@ llg_status kparams_from_ctx(const llg_ctx *c, KParams *out)
     Derived d;
     const llg_status s = derived_of(c, &d);
     if (s != LLG_OK) return s;
+    if (c->disp > 0.0) return fail(LLG_EUNSUPPORTED, "the dispersed-axis mode keeps its axes in the context");
     *out = kparams_of(d, c->nx, c->ny, c->nz, c->periodic, c->sw.dt);
     return LLG_OK;
 }
@@ -231,7 +281,7 @@ llg_status llg_create_grid(llg_ctx **out, int nx, int ny, int nz, double a0_m, i
 void llg_destroy(llg_ctx *c)
 {
     if (!c) return;
-    if (!c->d_status && !c->d_m && !c->d_flags) {  // nothing was ever put on the device
+    if (!c->d_status && !c->d_m && !c->d_flags && !c->d_axis) {  // nothing was ever put on the device
         delete c;
         return;
     }
@@ -243,6 +293,7 @@ void llg_destroy(llg_ctx *c)
     cudaFree(c->d_status);
     cudaFree(c->d_flags);
     cudaFree(c->d_slab);
+    cudaFree(c->d_axis);
     cudaGetLastError();
     delete c;
 }
@@ -264,7 +315,7 @@ llg_status llg_set_material(llg_ctx *c, double A0, double Ms, double K0, const d
         const double n = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
         if (!(n > 0.0)) return fail(LLG_EINVAL, "easy axis has zero length");
         if (std::fabs(u[0]) > 1e-12 * n || std::fabs(u[1]) > 1e-12 * n)
-            return fail(LLG_EUNSUPPORTED, "only an easy axis along z is built (axis dispersion is not)");
+            return fail(LLG_EUNSUPPORTED, "only an easy axis along z is built (a dispersed axis: llg_set_axis_dispersion)");
     }
     c->mat = llg::MaterialIn{A0, Ms, K0, alpha, T};
     c->has_material = true;
@@ -309,6 +360,47 @@ llg_status llg_set_cell_volume(llg_ctx *c, double volume_m3)
     if (!c) return fail(LLG_EINVAL, "ctx is NULL");
     if (!(volume_m3 >= 0.0) || !std::isfinite(volume_m3)) return fail(LLG_EINVAL, "volume must be >= 0");
     c->volume = volume_m3;
+    return LLG_OK;
+}
+
+llg_status llg_set_axis_dispersion(llg_ctx *c, double half_angle_rad)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (!(half_angle_rad >= 0.0) || !(half_angle_rad <= 0.5 * 3.141592653589793))
+        return fail(LLG_EINVAL, "the dispersion half-angle must lie in [0, pi/2]");
+    c->disp = half_angle_rad;
+    return LLG_OK;
+}
+
+llg_status llg_get_axes(llg_ctx *c, float *u)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (!u) return fail(LLG_EINVAL, "u is NULL");
+    if (c->n_real < 1 || !c->d_m) return fail(LLG_EINVAL, "no ensemble (llg_reset first)");
+    DeviceGuard g(c->device);
+    const size_t n = (size_t)c->n_real * (size_t)ncells_of(c);
+    const float4 *ax = nullptr;
+    llg_status s = ensure_axes(c, &ax);
+    if (s != LLG_OK) return s;
+    const bool dev = is_device_ptr(u);
+    if (!ax) {  // z-axis mode
+        if (dev) {
+            LLG_CUDA(cudaMemsetAsync(u, 0, n * 3 * sizeof(float), c->stream), "cudaMemsetAsync(u)");
+            LLG_CUDA(llg::fill_column(u, (int)n, 3, 2, 1.0f, c->stream), "fill +z");
+        } else {
+            for (size_t i = 0; i < n; ++i) {
+                u[3 * i] = 0.f;
+                u[3 * i + 1] = 0.f;
+                u[3 * i + 2] = 1.f;
+            }
+        }
+        return LLG_OK;
+    }
+    // float4 -> float3 rows through a strided 2-D copy
+    LLG_CUDA(cudaMemcpy2DAsync(u, 3 * sizeof(float), ax, sizeof(float4), 3 * sizeof(float), n,
+                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+             "axis copy");
+    if (!dev) LLG_CUDA(cudaStreamSynchronize(c->stream), "axis copy");
     return LLG_OK;
 }
 
@@ -388,6 +480,8 @@ llg_status llg_advance(llg_ctx *c, int64_t n_steps, float *m_samples)
     llg::KParams kp = llg::kparams_of(d, c->nx, c->ny, c->nz, c->periodic, c->sw.dt);
     kp.seed = c->seed;
     kp.real0 = c->real0;
+    s = ensure_axes(c, &kp.axis);
+    if (s != LLG_OK) return s;
     llg::RodPlan plan{};
     llg::SlabPlan splan{};
     const int eng = resolve_engine(c, kp, c->n_real, &plan, &splan);
@@ -548,6 +642,8 @@ llg_status llg_loop_area_grad(llg_ctx *c, int64_t n_steps, int objective, const 
     llg::KParams kp = llg::kparams_of(d, c->nx, c->ny, c->nz, c->periodic, c->sw.dt);
     kp.seed = c->seed;
     kp.real0 = c->real0;
+    s = ensure_axes(c, &kp.axis);
+    if (s != LLG_OK) return s;
     if (!llg::adjoint_supported(kp, c->device))
         return fail(LLG_EUNSUPPORTED, "the adjoint handles rods of at most 1024 cells with free faces");
     llg::RodPlan plan{};

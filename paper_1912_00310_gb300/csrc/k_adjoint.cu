@@ -13,6 +13,8 @@
 //               g_H~ = g_c1 x m~;  g_alpha += (m~ x c1).g_s1
 //   through H~: g_m~_i += c_ex sum_j g_H~_j (neighbours), g_m~_z += c_an g_H~_z;
 //               g_cex += g_H~.N(m~), g_can += g_H~_z m~_z, g_sigma += g_H~.xi
+//   (with a per-cell easy axis u the anisotropy term is c_an (m.u) u: g_m~ += c_an (g_H~.u) u and
+//   g_can += (g_H~.u)(m~.u))
 //   g_p = (g_m~ - m~(m~.g_m~))/|p|;  g_m += g_p;  g_s0 += -a g_p;  g_a += -s0.g_p
 //   through s0 and H: as through s1 and H~, with m, c0, H
 // and dL/dm of the previous state is g_m.  The host maps (g_alpha, g_a, g_cex, g_can, g_sigma)
@@ -60,6 +62,7 @@ __device__ __forceinline__ float3 nsum(const float4 *A, int q, int sy, int sz)
     return add3(nb, xyz(A[q + sz]));
 }
 
+template <bool AX>
 __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
     AdjParams ap, const float *__restrict__ ckpt, float *__restrict__ seg, float *__restrict__ lam,
     const double *__restrict__ w, double *__restrict__ partial)
@@ -86,6 +89,11 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
     const int n_rods = gridDim.x;
     float3 m = zero3a();
     if (act) m = make_float3(ckpt[rod_off + 3 * c], ckpt[rod_off + 3 * c + 1], ckpt[rod_off + 3 * c + 2]);
+    float3 u = make_float3(0.f, 0.f, 1.f);  // easy axis (dispersed-axis mode, AX)
+    if (AX && act) u = xyz(__ldg(p.axis + (size_t)rod * ncell + c));
+    auto field_of = [&](float3 nb, float3 mm, float3 hh, float Hz) {
+        return effective_field_sel<AX>(nb, mm, hh, p, Hz, u);
+    };
     __syncthreads();
 
     // ---- forward recomputation of the segment: seg[j] = state before step seg_start + j ----
@@ -107,7 +115,7 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
         __syncthreads();
         if (act) {
             h = thermal_field(p.seed, real, (uint32_t)c, n, p.sigma);
-            const float3 H = effective_field(nsum(M, q, sy, sz), m, h, p.c_ex, p.c_an, Hn);
+            const float3 H = field_of(nsum(M, q, sy, sz), m, h, Hn);
             const float3 s0 = llg_torque(m, H, p.alpha);
             P[q] = pad4(normalised(axpy(p.neg_dt_g1, s0, m)));
             acc = axpy(p.neg_hdt_g1, s0, m);
@@ -115,7 +123,7 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
         __syncthreads();
         if (act) {
             const float3 t = xyz(P[q]);
-            const float3 H = effective_field(nsum(P, q, sy, sz), t, h, p.c_ex, p.c_an, Hn1);
+            const float3 H = field_of(nsum(P, q, sy, sz), t, h, Hn1);
             m = normalised(axpy(p.neg_hdt_g1, llg_torque(t, H, p.alpha), acc));
         }
         __syncthreads();
@@ -154,7 +162,7 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
         if (act) {
             h = thermal_field(p.seed, real, (uint32_t)c, (unsigned long long)n, p.sigma);
             Nm = nsum(M, q, sy, sz);
-            H = effective_field(Nm, mi, h, p.c_ex, p.c_an, hn);
+            H = field_of(Nm, mi, h, hn);
             c0 = cross3(mi, H);
             s0 = llg_torque(mi, H, alpha);
             const float3 pv = axpy(p.neg_dt_g1, s0, mi);
@@ -167,7 +175,7 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
         float3 s1 = zero3a();
         if (act) {
             Nt = nsum(P, q, sy, sz);
-            Ht = effective_field(Nt, t, h, p.c_ex, p.c_an, hn1);
+            Ht = field_of(Nt, t, h, hn1);
             c1 = cross3(t, Ht);
             s1 = llg_torque(t, Ht, alpha);
             const float3 qv = axpy(p.neg_hdt_g1, add3(s0, s1), mi);
@@ -186,9 +194,15 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
         float3 gH = zero3a(), gm = zero3a();
         if (act) {
             gmt = axpy(p.c_ex, nsum(GT, q, sy, sz), gmt);
-            gmt.z = fmaf(p.c_an, gHt.z, gmt.z);
+            if constexpr (AX) {
+                const float gu = dot3(gHt, u);
+                gmt = axpy(p.c_an * gu, u, gmt);
+                g_can += (double)gu * (double)dot3(t, u);
+            } else {
+                gmt.z = fmaf(p.c_an, gHt.z, gmt.z);
+                g_can += (double)gHt.z * (double)t.z;
+            }
             g_cex += (double)dot3(gHt, Nt);
-            g_can += (double)gHt.z * (double)t.z;
             g_sigma += (double)dot3(gHt, h);  // d/dsigma = (1/sigma) g_H.h, divided on the host
             const float3 gp = scale3(1.f / pn, sub3(gmt, scale3(dot3(t, gmt), t)));
             gm = add3(gq, gp);                                     // q = m - ..., p = m - a s0
@@ -203,9 +217,15 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
         __syncthreads();
         if (act) {
             gm = axpy(p.c_ex, nsum(GH, q, sy, sz), gm);
-            gm.z = fmaf(p.c_an, gH.z, gm.z);
+            if constexpr (AX) {
+                const float gu = dot3(gH, u);
+                gm = axpy(p.c_an * gu, u, gm);
+                g_can += (double)gu * (double)dot3(mi, u);
+            } else {
+                gm.z = fmaf(p.c_an, gH.z, gm.z);
+                g_can += (double)gH.z * (double)mi.z;
+            }
             g_cex += (double)dot3(gH, Nm);
-            g_can += (double)gH.z * (double)mi.z;
             g_sigma += (double)dot3(gH, h);
             g = gm;
         }
@@ -260,10 +280,16 @@ cudaError_t adjoint_segment(const KParams &p, int n_real, long long seg_start, i
     ap.inj_scale = 1.0f / ((float)n_real * (float)p.ncells);
     const size_t rod_pad = (size_t)(p.nx + 2) * (p.ny + 2) * (p.nz + 2);
     const size_t smem = 4 * rod_pad * sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(adjoint_segment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const int threads = (p.ncells + 31) / 32 * 32;
-    adjoint_segment_kernel<<<n_real, threads, smem, st>>>(ap, ckpt, seg, lam, w, partial);
+    if (p.axis) {
+        cudaError_t e = cudaFuncSetAttribute(adjoint_segment_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        adjoint_segment_kernel<true><<<n_real, threads, smem, st>>>(ap, ckpt, seg, lam, w, partial);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(adjoint_segment_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        adjoint_segment_kernel<false><<<n_real, threads, smem, st>>>(ap, ckpt, seg, lam, w, partial);
+    }
     return cudaGetLastError();
 }
 

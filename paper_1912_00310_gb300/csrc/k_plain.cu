@@ -67,7 +67,8 @@ __global__ void plain_pred_kernel(KParams p, const float *__restrict__ m, float 
     const float3 mi = ld3(mr + 3 * (size_t)i);
     const float3 nb = neighbour_sum(mr, x, y, z, p);
     const float3 h = thermal_field(p.seed, p.real0 + (uint32_t)r, (uint32_t)i, n, p.sigma);
-    const float3 H = effective_field(nb, mi, h, p.c_ex, p.c_an, Hz);
+    const float3 H = p.axis ? effective_field_axis(nb, mi, h, p.c_ex, p.c_an, Hz, xyz(__ldg(p.axis + gid)))
+                            : effective_field(nb, mi, h, p.c_ex, p.c_an, Hz);
     const float3 s0 = llg_torque(mi, H, p.alpha);
     st3(mt + 3 * gid, normalised(axpy(p.neg_dt_g1, s0, mi)));
     st3(acc + 3 * gid, axpy(p.neg_hdt_g1, s0, mi));
@@ -87,7 +88,9 @@ __global__ void plain_corr_kernel(KParams p, float *__restrict__ m, const float 
     const float *tr = mt + (size_t)r * p.ncells * 3;
     const float3 ti = ld3(tr + 3 * (size_t)i);
     const float3 nb = neighbour_sum(tr, x, y, z, p);
-    const float3 H = effective_field(nb, ti, ld3(hth + 3 * gid), p.c_ex, p.c_an, Hz1);
+    const float3 h = ld3(hth + 3 * gid);
+    const float3 H = p.axis ? effective_field_axis(nb, ti, h, p.c_ex, p.c_an, Hz1, xyz(__ldg(p.axis + gid)))
+                            : effective_field(nb, ti, h, p.c_ex, p.c_an, Hz1);
     const float3 s1 = llg_torque(ti, H, p.alpha);
     st3(m + 3 * gid, normalised(axpy(p.neg_hdt_g1, s1, ld3(acc + 3 * gid))));
 }
@@ -105,6 +108,16 @@ __global__ void plain_sample_kernel(KParams p, const float *__restrict__ m, int 
         samples[(size_t)r * p.n_samples + k] = mean;
         if (!isfinite(mean)) atomicOr(status, 1);
     }
+}
+
+__global__ void axis_fill_kernel(float4 *__restrict__ ax, int n_real, int ncells, uint32_t seed,
+                                 uint32_t real0, float w_max)
+{
+    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (gid >= (long long)n_real * ncells) return;
+    const int r = (int)(gid / ncells);
+    const int c = (int)(gid - (long long)r * ncells);
+    ax[gid] = pad4(easy_axis(seed, real0 + (uint32_t)r, (uint32_t)c, w_max));
 }
 
 __global__ void fill_column_kernel(float *a, int rows, long long ld, long long col, float v)
@@ -146,6 +159,15 @@ cudaError_t fill_column(float *a, int rows, long long ld, long long col, float v
 {
     if (rows <= 0) return cudaSuccess;
     fill_column_kernel<<<(rows + 255) / 256, 256, 0, st>>>(a, rows, ld, col, v);
+    return cudaGetLastError();
+}
+
+cudaError_t axis_fill(float4 *ax, int n_real, int ncells, uint32_t seed, uint32_t real0, float w_max,
+                      cudaStream_t st)
+{
+    const long long n = (long long)n_real * ncells;
+    if (n <= 0) return cudaSuccess;
+    axis_fill_kernel<<<blocks_for(n), kThreads, 0, st>>>(ax, n_real, ncells, seed, real0, w_max);
     return cudaGetLastError();
 }
 

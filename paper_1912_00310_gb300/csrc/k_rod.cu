@@ -42,7 +42,7 @@ __device__ __forceinline__ float3 zero3() { return make_float3(0.f, 0.f, 0.f); }
 // ------------------------------------------------------------------------------------------
 // Shared memory: M[tot] and P[tot] float4 (x, y, z, 0), tot = rods_per_cta * (nx+2)(ny+2)(nz+2):
 // each rod padded by a zero ghost layer.
-template <int CPT>
+template <int CPT, bool AX>
 __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, float *__restrict__ m_glob,
                                                             int n_real, int rods_per_cta,
                                                             long long step0, long long n_steps,
@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, fl
     int pidx[CPT];
     uint32_t cell[CPT], real[CPT];
     bool act[CPT];
+    float3 uax[CPT];  // easy axes (dispersed-axis mode only)
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {
         const int i = threadIdx.x + k * T;
@@ -83,6 +84,10 @@ __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, fl
         pidx[k] = rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1);
         cell[k] = (uint32_t)c;
         real[k] = p.real0 + (uint32_t)(rod0 + rod);
+        uax[k] = zero3();
+        if constexpr (AX) {
+            if (act[k]) uax[k] = xyz(__ldg(p.axis + (size_t)(rod0 + rod) * ncell + c));
+        }
     }
     __syncthreads();
 
@@ -113,7 +118,7 @@ __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, fl
             nb = add3(nb, xyz(M[q + sy]));
             nb = add3(nb, xyz(M[q - sz]));
             nb = add3(nb, xyz(M[q + sz]));
-            const float3 H = effective_field(nb, mi, hth[k], p.c_ex, p.c_an, Hn);
+            const float3 H = effective_field_sel<AX>(nb, mi, hth[k], p, Hn, uax[k]);
             const float3 s0 = llg_torque(mi, H, p.alpha);
             P[q] = pad4(normalised(axpy(p.neg_dt_g1, s0, mi)));
             acc[k] = axpy(p.neg_hdt_g1, s0, mi);
@@ -129,7 +134,7 @@ __global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, fl
             nb = add3(nb, xyz(P[q + sy]));
             nb = add3(nb, xyz(P[q - sz]));
             nb = add3(nb, xyz(P[q + sz]));
-            const float3 H = effective_field(nb, ti, hth[k], p.c_ex, p.c_an, Hn1);
+            const float3 H = effective_field_sel<AX>(nb, ti, hth[k], p, Hn1, uax[k]);
             const float3 s1 = llg_torque(ti, H, p.alpha);
             M[q] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[k])));
             hpre[k] = thermal_field(p.seed, real[k], cell[k], n + 1, p.sigma);
@@ -183,7 +188,7 @@ __host__ __device__ constexpr int pipelined_max_threads(int R)
     return R == 1 ? 768 : (R == 2 ? 672 : (R == 3 ? 512 : 384));
 }
 
-template <int R>
+template <int R, bool AX>
 __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_kernel(KParams p, float *__restrict__ m_glob,
                                                                long long step0, long long n_steps,
                                                                float *__restrict__ samples,
@@ -225,6 +230,7 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_ker
         cbase[j] = (uint32_t)(rr * nx);  // cell index x + nx * (y + ny * z), rr = y + ny * z
     }
     const PhiloxKeys keys = philox_keys(p.seed, p.real0 + (uint32_t)rod);
+    const float4 *axr = AX ? p.axis + (size_t)rod * ncell : nullptr;  // this rod's easy axes
 
     float3 mprev[R], mcur[R], mta[R], mtb[R], acc[R], hth[R];
 #pragma unroll
@@ -267,7 +273,8 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_ker
                 nb = axpy(wp[j], xyz(Mp[qq + 1]), nb);
                 nb = add3(nb, xyz(Mp[qq - ny]));
                 nb = add3(nb, xyz(Mp[qq + ny]));
-                const float3 H = effective_field(nb, mcur[j], h_new[j], p.c_ex, p.c_an, Hp);
+                const float3 u = AX ? xyz(__ldg(axr + cbase[j] + xp)) : zero3();
+                const float3 H = effective_field_sel<AX>(nb, mcur[j], h_new[j], p, Hp, u);
                 const float3 s0 = llg_torque(mcur[j], H, p.alpha);
                 mt_new[j] = normalised(axpy(p.neg_dt_g1, s0, mcur[j]));
                 acc_new[j] = axpy(p.neg_hdt_g1, s0, mcur[j]);
@@ -290,7 +297,8 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_ker
                 nb = axpy(wp[j], xyz(Sr[qq + 1]), nb);
                 nb = add3(nb, xyz(Sr[qq - ny]));
                 nb = add3(nb, xyz(Sr[qq + ny]));
-                const float3 H = effective_field(nb, mtb[j], hth[j], p.c_ex, p.c_an, Hc);
+                const float3 u = AX ? xyz(__ldg(axr + cbase[j] + xc)) : zero3();
+                const float3 H = effective_field_sel<AX>(nb, mtb[j], hth[j], p, Hc, u);
                 const float3 s1 = llg_torque(mtb[j], H, p.alpha);
                 Mw[qq] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[j])));
             }
@@ -788,10 +796,17 @@ cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_r
     if (plan.kind == 1) {
 #define LLG_TWOPHASE(C)                                                                         \
     case C:                                                                                     \
-        e = set_smem(rod_twophase_kernel<C>, plan.smem_bytes);                                  \
-        if (e != cudaSuccess) return e;                                                         \
-        rod_twophase_kernel<C><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(               \
-            p, m, n_real, plan.rods_per_cta, step0, n_steps, samples, status);                  \
+        if (p.axis) {                                                                           \
+            e = set_smem(rod_twophase_kernel<C, true>, plan.smem_bytes);                        \
+            if (e != cudaSuccess) return e;                                                     \
+            rod_twophase_kernel<C, true><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(     \
+                p, m, n_real, plan.rods_per_cta, step0, n_steps, samples, status);              \
+        } else {                                                                                \
+            e = set_smem(rod_twophase_kernel<C, false>, plan.smem_bytes);                       \
+            if (e != cudaSuccess) return e;                                                     \
+            rod_twophase_kernel<C, false><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(    \
+                p, m, n_real, plan.rods_per_cta, step0, n_steps, samples, status);              \
+        }                                                                                       \
         break;
         switch (plan.cells_per_thread) {
             LLG_TWOPHASE(1)
@@ -804,14 +819,19 @@ cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_r
     } else if (plan.kind == 2) {
 #define LLG_PIPELINED(R)                                                                        \
     case R:                                                                                     \
-        if (p.nx == 8 && p.ny == 24 && p.nz == 56 && !plan.generic) {                           \
+        if (p.axis) {                                                                           \
+            e = set_smem(rod_pipelined_kernel<R, true>, plan.smem_bytes);                       \
+            if (e != cudaSuccess) return e;                                                     \
+            rod_pipelined_kernel<R, true><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(    \
+                p, m, step0, n_steps, samples, status);                                         \
+        } else if (p.nx == 8 && p.ny == 24 && p.nz == 56 && !plan.generic) {                    \
             e = launch_nx<R, 8, 24, 56>(p, plan, m, n_real, step0, n_steps, samples, status, flags, st); \
         } else if (p.nx == 8 && !plan.generic) {                                                \
             e = launch_nx<R, 8>(p, plan, m, n_real, step0, n_steps, samples, status, flags, st); \
         } else {                                                                                \
-            e = set_smem(rod_pipelined_kernel<R>, plan.smem_bytes);                             \
+            e = set_smem(rod_pipelined_kernel<R, false>, plan.smem_bytes);                      \
             if (e != cudaSuccess) return e;                                                     \
-            rod_pipelined_kernel<R><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(          \
+            rod_pipelined_kernel<R, false><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(   \
                 p, m, step0, n_steps, samples, status);                                         \
         }                                                                                       \
         break;

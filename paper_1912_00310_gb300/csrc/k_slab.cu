@@ -48,7 +48,7 @@ __device__ __forceinline__ bool wrap(int &v, int n, bool periodic)
     return true;
 }
 
-template <int CPT>
+template <int CPT, bool AX>
 __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, SlabGeom G,
                                                                     const float4 *__restrict__ min,
                                                                     float4 *__restrict__ mout,
@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
     const float4 *src = min + (size_t)real * plane_cells * G.NZ;
     float4 *dst = mout + (size_t)real * plane_cells * G.NZ;
     const PhiloxKeys keys = philox_keys(p.seed, p.real0 + (uint32_t)real);
+    const float4 *axr = AX ? p.axis + (size_t)real * plane_cells * G.NZ : nullptr;  // easy axes
     Sweep sw;
     sw.init((long long)n, p);
     const float Hn = sw.value();
@@ -175,7 +176,8 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
                 nb = add3(nb, xyz(Mz[q + pitch]));
                 nb = add3(nb, mA[k]);
                 nb = add3(nb, mnext);
-                const float3 H = effective_field(nb, mB[k], hnew[k], p.c_ex, p.c_an, Hn);
+                const float3 u = AX ? xyz(__ldg(axr + cell[k] + zoff)) : zero3s();
+                const float3 H = effective_field_sel<AX>(nb, mB[k], hnew[k], p, Hn, u);
                 const float3 s0 = llg_torque(mB[k], H, p.alpha);
                 tnew[k] = normalised(axpy(p.neg_dt_g1, s0, mB[k]));
                 anew[k] = axpy(p.neg_hdt_g1, s0, mB[k]);
@@ -194,7 +196,8 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
                     nb = add3(nb, xyz(Mz[q + pitch]));
                     nb = add3(nb, rA);
                     nb = add3(nb, rnext);
-                    const float3 H = effective_field(nb, rB, h, p.c_ex, p.c_an, Hn);
+                    const float3 u = AX ? xyz(__ldg(axr + rcell + zoff)) : zero3s();
+                    const float3 H = effective_field_sel<AX>(nb, rB, h, p, Hn, u);
                     rt = normalised(axpy(p.neg_dt_g1, llg_torque(rB, H, p.alpha), rB));
                 }
                 Tw[rpos] = pad4(rt);
@@ -217,7 +220,8 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
                 nb = add3(nb, xyz(Tr[t + pitch]));
                 nb = add3(nb, tA[k]);
                 nb = add3(nb, tnext);
-                const float3 H = effective_field(nb, tB[k], hth[k], p.c_ex, p.c_an, Hn1);
+                const float3 u = AX ? xyz(__ldg(axr + cell[k] + plane_cells * (size_t)zc)) : zero3s();
+                const float3 H = effective_field_sel<AX>(nb, tB[k], hth[k], p, Hn1, u);
                 const float3 s1 = llg_torque(tB[k], H, p.alpha);
                 out[cell[k]] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[k])));
             }
@@ -347,10 +351,17 @@ cudaError_t slab_advance(const KParams &p, const SlabPlan &plan, float *m, int n
     long long count = 1;
 #define LLG_SLAB(C)                                                                                   \
     case C:                                                                                           \
-        e = cudaFuncSetAttribute(slab_step_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                 (int)plan.smem_bytes);                                               \
-        if (e != cudaSuccess) return e;                                                               \
-        slab_step_kernel<C><<<grid, plan.threads, plan.smem_bytes, st>>>(p, G, a, b, n);              \
+        if (p.axis) {                                                                                 \
+            e = cudaFuncSetAttribute(slab_step_kernel<C, true>,                                       \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem_bytes); \
+            if (e != cudaSuccess) return e;                                                           \
+            slab_step_kernel<C, true><<<grid, plan.threads, plan.smem_bytes, st>>>(p, G, a, b, n);    \
+        } else {                                                                                      \
+            e = cudaFuncSetAttribute(slab_step_kernel<C, false>,                                      \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem_bytes); \
+            if (e != cudaSuccess) return e;                                                           \
+            slab_step_kernel<C, false><<<grid, plan.threads, plan.smem_bytes, st>>>(p, G, a, b, n);   \
+        }                                                                                             \
         break;
     for (long long s = 0; s < n_steps; ++s) {
         const long long n = step0 + s;

@@ -40,6 +40,9 @@ struct KParams {
     uint32_t real0;           // key of realisation 0 of this ensemble
     long long sample_every;   // 0: no sampling
     long long n_samples;      // columns of the sample array
+    // per-cell easy axes [n_real][ncells] (x, y, z, 0) of the dispersed-axis mode, or NULL for
+    // the axis z in every cell; indexed by the rod's position in this ensemble
+    const float4 *axis;
 };
 
 // Host helpers (scaling.cpp)
@@ -82,6 +85,9 @@ cudaError_t plain_advance(const KParams &p, float *m, float *mt, float *acc, flo
 
 // a[r * ld + col] = v for r in [0, rows)
 cudaError_t fill_column(float *a, int rows, long long ld, long long col, float v, cudaStream_t st);
+// ax[r][c] = easy_axis(seed, real0 + r, c, w_max) for r < n_real, c < ncells
+cudaError_t axis_fill(float4 *ax, int n_real, int ncells, uint32_t seed, uint32_t real0, float w_max,
+                      cudaStream_t st);
 
 // ---- resident engine (k_rod.cu): rods in shared memory for the whole launch ------------------
 struct RodPlan {

@@ -150,6 +150,42 @@ __device__ __forceinline__ float3 effective_field(float3 nb, float3 m, float3 ht
                        fmaf(c_ex, nb.z, fmaf(c_an, m.z, hth.z + Hz)));
 }
 
+// Effective field with a per-cell easy axis u (the dispersed-axis mode):
+// c_ex nb + h_th + c_an (m.u) u + Hz z.  A separate form, not effective_field with u = z: the
+// z-axis form fuses c_an m_z into one rounding, which keeps the default path unchanged.
+__device__ __forceinline__ float3 effective_field_axis(float3 nb, float3 m, float3 hth, float c_ex,
+                                                       float c_an, float Hz, float3 u)
+{
+    const float a = c_an * fmaf(m.x, u.x, fmaf(m.y, u.y, m.z * u.z));
+    return make_float3(fmaf(c_ex, nb.x, fmaf(a, u.x, hth.x)), fmaf(c_ex, nb.y, fmaf(a, u.y, hth.y)),
+                       fmaf(c_ex, nb.z, fmaf(a, u.z, hth.z + Hz)));
+}
+
+// The effective field of the z-axis mode (AX = false; u unused) or of the dispersed-axis mode.
+template <bool AX>
+__device__ __forceinline__ float3 effective_field_sel(float3 nb, float3 m, float3 hth, const KParams &p,
+                                                      float Hz, float3 u)
+{
+    if constexpr (AX)
+        return effective_field_axis(nb, m, hth, p.c_ex, p.c_an, Hz, u);
+    else
+        return effective_field(nb, m, hth, p.c_ex, p.c_an, Hz);
+}
+
+// Easy axis of one cell of one realisation: uniform over the solid angle of the cone of
+// half-angle theta_max about z, drawn from Philox4x32-10 with key (seed, realisation) and counter
+// (cell, 0, 0, 1) (the thermal draws use tag word 0).  w_max = 1 - cos(theta_max); on a
+// spherical cap 1 - cos(theta) is uniform on [0, w_max] and the azimuth is uniform.
+__device__ __forceinline__ float3 easy_axis(uint32_t seed, uint32_t real, uint32_t cell, float w_max)
+{
+    const uint4 x = philox4x32_10(make_uint4(cell, 0u, 0u, 1u), seed, real);
+    const float w = w_max * uniform24(x.x);
+    float sp, cp;
+    sincospif(2.0f * uniform24(x.y), &sp, &cp);
+    const float st = sqrtf(w * (2.0f - w));
+    return make_float3(st * cp, st * sp, 1.0f - w);
+}
+
 // Zeeman field along z at step n, tracked by its phase (n mod period) in steps:
 //   shape 0: triangle, H0 + slope * tri(ph) with tri = ph for ph <= n_half, period - ph after
 //            (period = 2 n_half; n_half = 0 holds H0);

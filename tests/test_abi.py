@@ -103,6 +103,10 @@ def test_sweep_validation(pkg):
     assert e.value.status == 1
     with pytest.raises(pkg.LLGError):
         g.set_cell_volume(-1.0)
+    with pytest.raises(pkg.LLGError) as e:
+        g.set_axis_dispersion(-0.1)
+    assert e.value.status == 1
+    g.set_axis_dispersion(0.0872664626)
     with pytest.raises(pkg.LLGError):
         g.set_material(A0=1e-11, Ms=4.8e5, K0=1e4, alpha=0.1, T=310, u=(0.1, 0, 1))
     with pytest.raises(pkg.LLGError):

@@ -1,6 +1,6 @@
-"""GPU parity of the paper's own field protocol: the sinusoidal field H_max sin(2 pi f t) with
-SR = 4 H_max f (started at +H_max), and the single-block limit (the whole rod as one macrospin of
-volume 10752 a0^3 at b = 22, no exchange).
+"""GPU parity of the paper's own protocol: the sinusoidal field H_max sin(2 pi f t) with
+SR = 4 H_max f (started at +H_max), the single-block limit (the whole rod as one macrospin of
+volume 10752 a0^3 at b = 22, no exchange) and the 5-degree dispersion of the easy axis.
 
 Every engine evaluates the field from the same integer phase, so the engines stay bitwise equal;
 against the FP64 oracle the trajectories stay within 1e-4 over the first 1000 steps, past a
@@ -186,4 +186,116 @@ def test_single_block_trajectory_and_loop(pkg, orc):
         se = math.hypot(o[key + "_se"], mine[key + "_se"])
         assert abs(o[key] - mine[key]) <= 3 * se, (key, o[key], mine[key], se)
     assert 117 < mine["Hc"] < 400  # above the Stoner-Wohlfarth field 2K/(mu0 Ms), below H_max
+    g.close()
+
+
+# ---- the 5-degree easy-axis dispersion --------------------------------------------------------
+DISP5 = math.radians(5.0)
+
+
+def disp_grid(pkg, dims, b, *, engine, kind=0, disp=DISP5, periodic=0, dt=None):
+    g = sine_grid(pkg, dims, b, engine=engine, kind=kind, periodic=periodic, dt=dt)
+    g.set_axis_dispersion(disp)
+    return g
+
+
+def disp_problem(orc, dims, b, disp=DISP5, periodic=0, dt=None):
+    p = sine_problem(orc, dims, b, periodic=periodic, dt=dt)
+    p.disp = disp
+    return p
+
+
+def test_axes_match_oracle(pkg, orc):
+    dims, b = ROD_DIMS[4], 4
+    g = disp_grid(pkg, dims, b, engine=pkg.ENGINE_RESIDENT)
+    g.reset(seed=5, n_real=3, real_offset=40)
+    u = np.zeros((3, g.ncells, 3), dtype=np.float32)
+    g.get_axes(u)
+    ref = orc.easy_axes(disp_problem(orc, dims, b), seed=5, n_real=3, real0=40)
+    assert np.max(np.abs(u - ref)) < 1e-6
+    d = torch.empty((3, g.ncells, 3), device="cuda")
+    g.get_axes(d)
+    g.sync(60)
+    assert np.array_equal(d.cpu().numpy(), u)
+    g.set_axis_dispersion(0.0)
+    g.get_axes(u)
+    assert np.array_equal(u, np.broadcast_to(np.float32([0, 0, 1]), u.shape))
+    g.close()
+
+
+def test_dispersion_engines_bitwise_and_oracle(pkg, orc):
+    """A wide (0.3 rad) dispersion so that the axes matter within 1000 steps."""
+    dims, b, n_real = ROD_DIMS[4], 4, 3
+    p = disp_problem(orc, dims, b, disp=0.3)
+    ref = orc.uniform_state(n_real, p.ncells)
+    orc.run(p, ref, seed=0, n_steps=1000)
+    z = orc.uniform_state(n_real, p.ncells)
+    orc.run(sine_problem(orc, dims, b), z, seed=0, n_steps=1000)
+    assert np.max(np.abs(ref - z)) > 1e-3  # the dispersion moves the trajectory by far more than 1e-4
+    states = []
+    for name, kind in ENGINES:
+        g = disp_grid(pkg, dims, b, engine=_engine(pkg, name), kind=kind, disp=0.3)
+        g.reset(seed=0, n_real=n_real)
+        g.advance(1000)
+        s = state_of(g, n_real)
+        assert float(np.max(np.abs(s.double().cpu().numpy() - ref))) <= 1e-4, (name, kind)
+        states.append(s)
+        g.close()
+    for s in states[1:]:
+        assert torch.equal(s, states[0])
+
+
+def test_dispersion_b1_rod_and_periodic_slab(pkg, orc):
+    """The full b = 1 rod (generic plane-pipelined kernel with axes) and a periodic slab through
+    the streaming engine, against the oracle and the plain engine."""
+    dims, n_real = ROD_DIMS[1], 2
+    g = disp_grid(pkg, dims, 1, engine=pkg.ENGINE_RESIDENT, dt=2e-15)
+    g.reset(seed=4, n_real=n_real)
+    g.advance(300)
+    p = disp_problem(orc, dims, 1, dt=2e-15)
+    ref = orc.uniform_state(n_real, p.ncells)
+    orc.run(p, ref, seed=4, n_steps=300)
+    assert float(np.max(np.abs(state_of(g, n_real).double().cpu().numpy() - ref))) <= 1e-4
+    g.close()
+    dims = (40, 45, 6)
+    a = disp_grid(pkg, dims, 1, engine=pkg.ENGINE_STREAM, periodic=0b011, dt=2e-15, disp=0.3)
+    c = disp_grid(pkg, dims, 1, engine=pkg.ENGINE_PLAIN, periodic=0b011, dt=2e-15, disp=0.3)
+    for x in (a, c):
+        x.reset(seed=6, n_real=1)
+        x.advance(200)
+    assert torch.equal(state_of(a, 1), state_of(c, 1))
+    a.close()
+    c.close()
+
+
+def test_dispersion_batch_equals_job_alone(pkg):
+    dims, b = ROD_DIMS[4], 4
+    jobs = [disp_grid(pkg, dims, b, engine=pkg.ENGINE_RESIDENT, disp=d) for d in (0.3, 0.0)]
+    for i, j in enumerate(jobs):
+        j.reset(seed=8 + i, n_real=5)
+    pkg.run_batch(jobs, 500)
+    for i, d in enumerate((0.3, 0.0)):
+        alone = disp_grid(pkg, dims, b, engine=pkg.ENGINE_RESIDENT, disp=d)
+        alone.reset(seed=8 + i, n_real=5)
+        alone.advance(500)
+        assert torch.equal(state_of(jobs[i], 5), state_of(alone, 5)), d
+        alone.close()
+    for j in jobs:
+        j.close()
+
+
+def test_dispersion_adjoint_matches_oracle_gradient(pkg, orc):
+    dims, n_real, step0, n_steps = (1, 2, 3), 16, 130, 640
+    g = disp_grid(pkg, dims, 4, engine=pkg.ENGINE_RESIDENT, disp=0.3)
+    g.reset(seed=0, n_real=n_real)
+    m0 = random_unit_state(n_real, 6, seed=5, cone=0.6).astype(np.float32)
+    g.set_state(m0, step0)
+    target = 0.5 * np.cos(2 * np.pi * np.arange(g.n_samples) / (g.n_samples - 1))
+    L, grad = g.loss_grad(n_steps, target, objective=0, ckpt_every=256)
+    p = disp_problem(orc, dims, 4, disp=0.3)
+    Lo, go, _ = orc.loss_grad(p, m0.astype(np.float64), target=target, scale=(1.0, 1.0, 1.0),
+                              seed=0, step0=step0, n_steps=n_steps, sample_every=g.sample_every)
+    assert L == pytest.approx(Lo, rel=1e-3)
+    for k in range(3):
+        assert grad[k] == pytest.approx(go[k], rel=1e-2, abs=1e-3 * np.abs(go).max()), (k, grad, go)
     g.close()
