@@ -5,10 +5,13 @@ axis, driven by a sinusoidal field of amplitude 500 Oe at a sweep rate SR = 4 H_
 the single-block limit b = 22 (the whole rod as one prism of volume 10752 a0^3).
 
 The paper prints the rescaled loop areas 495, 488, 443, 432 and 472 Oe for b = 1, 2, 4, 8, 22
-(the text accompanying Fig. 2c).  `run` computes one level's ensemble of loops on the GPU through
-the library's C ABI and returns its observables next to the printed area.
+(the text accompanying Fig. 2c), and for the SR/alpha invariance of Fig. 4 (loops at several
+sweep-rate and damping pairs with SR/alpha = 2.5 Oe/ns) a mean area of 171.3 +- 2.8 Oe at b = 4
+and 149.4 Oe at b = 8.  `run` computes one level's ensemble of loops on the GPU through the
+library's C ABI and returns its observables next to the printed area.
 
     python -m paper_1912_00310_gb300.protocol --b 8 4 22 --n-real 256
+    python -m paper_1912_00310_gb300.protocol --b 4 8 --rates 2.5 5 10 25 --sr-over-alpha 2.5
 
 Differences from the paper's runs: the time step grows with b (2, 5, 10, 20, 20 fs for
 b = 1, 2, 4, 8, 22; the paper quotes 1 fs), the loop is the first cycle from m = +z at +H_max,
@@ -29,6 +32,7 @@ ROD_CELLS = (8, 24, 56)                     # the rod in cells of a0
 BLOCK_B = 22                                # the single-block level
 DT_BY_B = {1: 2e-15, 2: 5e-15, 4: 10e-15, 8: 20e-15, BLOCK_B: 20e-15}
 PAPER_AREA_OE = {1: 495.0, 2: 488.0, 4: 443.0, 8: 432.0, BLOCK_B: 472.0}
+PAPER_AREA_SR_ALPHA_2P5_OE = {4: 171.3, 8: 149.4}  # Fig. 4 text, SR/alpha = 2.5 Oe/ns
 
 
 def level_grid(b: int):
@@ -58,7 +62,7 @@ def make_grid(b: int, *, H_max=500.0, rate=2.5, dt=None, alpha=None, disp_deg=5.
     return g
 
 
-def run(b: int, n_real: int, seed: int = 0, *, tune=True, **kw) -> dict:
+def run(b: int, n_real: int, seed: int = 0, *, tune=True, paper=PAPER_AREA_OE, **kw) -> dict:
     """One loop per realisation at level b; the loop observables (jackknife standard errors)
     with the rescaled area beside the paper's."""
     g = make_grid(b, **kw)
@@ -74,7 +78,9 @@ def run(b: int, n_real: int, seed: int = 0, *, tune=True, **kw) -> dict:
                    dt_s=kw.get("dt") or DT_BY_B[b], seconds=sec,
                    cell_steps_per_s=g.ncells * n_real * g.steps_per_loop / sec)
         out.update(st)
-        out["paper_area0_Oe"] = PAPER_AREA_OE.get(b)
+        out["rate_Oe_per_ns"] = kw.get("rate", 2.5)
+        out["alpha"] = MAGNETITE["alpha"] if kw.get("alpha") is None else kw["alpha"]
+        out["paper_area0_Oe"] = paper.get(b)
         if out["paper_area0_Oe"]:
             out["area0_over_paper"] = out["area0_Oe"] / out["paper_area0_Oe"]
         return out
@@ -88,13 +94,25 @@ def main(argv=None):
     ap.add_argument("--n-real", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--rate", type=float, default=2.5, help="sweep rate SR = 4 H_max f (Oe/ns)")
+    ap.add_argument("--rates", type=float, nargs="+", default=None,
+                    help="several sweep rates, each with alpha = rate / --sr-over-alpha")
+    ap.add_argument("--sr-over-alpha", type=float, default=None)
     ap.add_argument("--h-max", type=float, default=500.0)
     ap.add_argument("--alpha", type=float, default=None)
     ap.add_argument("--disp-deg", type=float, default=5.0)
     a = ap.parse_args(argv)
+    pairs = [(a.rate, a.alpha)]
+    paper = PAPER_AREA_OE
+    if a.rates:
+        if not a.sr_over_alpha:
+            ap.error("--rates needs --sr-over-alpha")
+        pairs = [(r, r / a.sr_over_alpha) for r in a.rates]
+        paper = PAPER_AREA_SR_ALPHA_2P5_OE if a.sr_over_alpha == 2.5 else {}
     for b in a.b:
-        r = run(b, a.n_real, a.seed, H_max=a.h_max, rate=a.rate, alpha=a.alpha, disp_deg=a.disp_deg)
-        print(json.dumps(r), flush=True)
+        for rate, alpha in pairs:
+            r = run(b, a.n_real, a.seed, paper=paper, H_max=a.h_max, rate=rate, alpha=alpha,
+                    disp_deg=a.disp_deg)
+            print(json.dumps(r), flush=True)
 
 
 if __name__ == "__main__":
