@@ -144,6 +144,17 @@ llg_status llg_set_axis_dispersion(llg_ctx *ctx, double half_angle_rad);
  * return; a device copy is ordered on the context's stream.  Errors: EINVAL (no ensemble). */
 llg_status llg_get_axes(llg_ctx *ctx, float *u);
 
+/* The Grinstein-Koch flow of the reduced parameters (Eqs. 4-7) integrated numerically from
+ * l = 0 to l = ln b (classical Runge-Kutta, n_steps equal steps, host FP64):
+ * with Ts the reduced temperature T star = k_B T Lambda / A, h = mu0 Ms H / (A Lambda^2) and
+ * g = K / (A Lambda^2), Lambda = 2 pi / a: d(Ts)/dl = (F - 1) Ts, dh/dl = 2 h,
+ * dg/dl = (2 - 2F) g, F = Ts / (2 pi (1 + h + g)).
+ * out = {Ts(ln b), h(ln b), g(ln b), zeta(ln b) = exp(-integral of F)}.  The scaling modes use
+ * the closed form zeta = t/b + 1 - t that this flow reduces to when h = g = 0 (t = Ts(0) / 2 pi);
+ * this call measures the difference for a material.  Needs no context or GPU.
+ * Errors: EINVAL (b < 1, n_steps < 1, a negative parameter). */
+llg_status llg_gk_flow(double Tstar0, double h0, double g0, double b, int64_t n_steps, double out[4]);
+
 /* Select the integration engine (llg_engine).  Errors: EINVAL, EUNSUPPORTED (the engine cannot
  * hold this grid: checked at the next reset/advance). */
 llg_status llg_set_engine(llg_ctx *ctx, int engine);

@@ -116,6 +116,42 @@ double orc_m_rescale(int mode, double zeta, double delta)
     return 1.0;
 }
 
+/* Grinstein-Koch flow of the reduced parameters with l = ln b (Eqs. 4-7), writing Ts for the
+ * reduced temperature T star:
+ *   d(Ts)/dl = (-1 + F) Ts,  dh/dl = 2 h,  dg/dl = (2 - 2 F) g,  F = Ts / (2 pi (1 + h + g)),
+ * and the magnetisation factor zeta(l) = exp(-integral_0^l F dl').  Classical fourth-order
+ * Runge-Kutta over n equal steps of l from 0 to ln b, the integral of F carried as a fourth
+ * state variable.  out = {Ts(l), h(l), g(l), zeta(l)}. */
+static void gk_derivative(const double y[4], double d[4])
+{
+    const double F = y[0] / (2.0 * ORC_PI * (1.0 + y[1] + y[2]));
+    d[0] = (-1.0 + F) * y[0];
+    d[1] = 2.0 * y[1];
+    d[2] = (2.0 - 2.0 * F) * y[2];
+    d[3] = F;
+}
+
+void orc_gk_flow(double Ts0, double h0, double g0, double b, int64_t n, double out[4])
+{
+    double y[4] = {Ts0, h0, g0, 0.0};
+    const double dl = log(b) / (double)n;
+    for (int64_t s = 0; s < n; ++s) {
+        double k1[4], k2[4], k3[4], k4[4], t[4];
+        gk_derivative(y, k1);
+        for (int i = 0; i < 4; ++i) t[i] = y[i] + 0.5 * dl * k1[i];
+        gk_derivative(t, k2);
+        for (int i = 0; i < 4; ++i) t[i] = y[i] + 0.5 * dl * k2[i];
+        gk_derivative(t, k3);
+        for (int i = 0; i < 4; ++i) t[i] = y[i] + dl * k3[i];
+        gk_derivative(t, k4);
+        for (int i = 0; i < 4; ++i) y[i] += dl / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+    }
+    out[0] = y[0];
+    out[1] = y[1];
+    out[2] = y[2];
+    out[3] = exp(-y[3]);
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Problem description.  All quantities are the simulation-level values (already rescaled).    */
 /* ------------------------------------------------------------------------------------------ */

@@ -61,6 +61,7 @@ def lib():
             L.orc_zeta.argtypes = [C.c_double] * 3
             L.orc_zeta.restype = C.c_double
             L.orc_easy_axis.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, dp]
+            L.orc_gk_flow.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int64, dp]
             L.orc_exchange_length.argtypes = [C.c_double] * 3
             L.orc_exchange_length.restype = C.c_double
             L.orc_m_rescale.argtypes = [C.c_int, C.c_double, C.c_double]
@@ -128,6 +129,22 @@ def easy_axes(p: Problem, seed: int, n_real: int, real0: int = 0) -> np.ndarray:
             L.orc_easy_axis(C.byref(pc), seed & 0xFFFFFFFF, (real0 + r) & 0xFFFFFFFF, i,
                             _dp(out[r, i]))
     return out
+
+
+def gk_flow(Tstar0: float, h0: float, g0: float, b: float, n: int = 4000) -> dict:
+    """Grinstein-Koch flow (Eqs. 4-7) from l = 0 to ln b: reduced temperature T*, field h and
+    anisotropy g at level b and the magnetisation factor zeta."""
+    out = np.zeros(4)
+    lib().orc_gk_flow(Tstar0, h0, g0, b, int(n), _dp(out))
+    return dict(zip(["Tstar", "h", "g", "zeta"], out.tolist()))
+
+
+def reduced_parameters(*, T, A, K, Ms, H_Oe, a):
+    """Eqs. 4-5: T* = k_B T Lambda / A, h = mu0 Ms H / (A Lambda^2) (H in Oe converted to A/m),
+    g = K / (A Lambda^2), with the cut-off Lambda = 2 pi / a of cells of edge a."""
+    lam = 2.0 * math.pi / a
+    return dict(Tstar=KB * T * lam / A, h=MU0 * Ms * H_Oe * OE / (A * lam * lam),
+                g=K / (A * lam * lam))
 
 
 def zeta(b: float, T: float, Tc: float) -> float:

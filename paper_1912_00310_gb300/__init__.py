@@ -15,7 +15,7 @@ from ._lib import (COEFF_NAMES, ENGINE_AUTO, ENGINE_PLAIN, ENGINE_RESIDENT, ENGI
                    TUNE_ROWS_PER_THREAD, LLGError,
                    LoopStats)
 
-__all__ = ["Grid", "run_batch", "loop_loss", "LLGError", "LoopStats", "loop_stats", "ENGINE_AUTO", "ENGINE_RESIDENT",
+__all__ = ["Grid", "run_batch", "loop_loss", "LLGError", "LoopStats", "loop_stats", "gk_flow", "ENGINE_AUTO", "ENGINE_RESIDENT",
            "ENGINE_PLAIN", "ENGINE_STREAM", "TUNE_ROD_KIND", "TUNE_RODS_PER_CTA", "TUNE_CHUNK_STEPS",
            "TUNE_ROWS_PER_THREAD", "TUNE_GENERIC_KERNEL", "TUNE_BALANCE",
            "library"]
@@ -242,6 +242,13 @@ def loop_loss(scales, grid, *, seed, n_real, n_steps, target=None, objective=0, 
     """Differentiable loop loss (torch autograd) of the calibration scale factors."""
     return _loop_loss_function().apply(scales, grid, seed, n_real, n_steps, target, objective,
                                        ckpt_every, mode, Tc, delta)
+
+
+def gk_flow(Tstar0: float, h0: float, g0: float, b: float, n_steps: int = 4000) -> dict:
+    """The Grinstein-Koch flow (Eqs. 4-7) from l = 0 to ln b: {Tstar, h, g, zeta}."""
+    out = (C.c_double * 4)()
+    _lib.check(_lib.load().llg_gk_flow(Tstar0, h0, g0, b, int(n_steps), out))
+    return dict(zip(["Tstar", "h", "g", "zeta"], list(out)))
 
 
 def loop_stats(samples: np.ndarray, H: np.ndarray, k_turn: int, mode=1, zeta=1.0, delta=0.511):

@@ -54,6 +54,7 @@ SIGNATURES = {
     "llg_set_engine": (C.c_int, [_vp, C.c_int]),
     "llg_set_cell_volume": (C.c_int, [_vp, C.c_double]),
     "llg_set_axis_dispersion": (C.c_int, [_vp, C.c_double]),
+    "llg_gk_flow": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int64, _vp]),
     "llg_get_axes": (C.c_int, [_vp, _vp]),
     "llg_set_tuning": (C.c_int, [_vp, C.c_int, _i64]),
     "llg_reset": (C.c_int, [_vp, C.c_uint32, C.c_int, C.c_uint32]),

@@ -363,6 +363,15 @@ llg_status llg_set_cell_volume(llg_ctx *c, double volume_m3)
     return LLG_OK;
 }
 
+llg_status llg_gk_flow(double Tstar0, double h0, double g0, double b, int64_t n_steps, double out[4])
+{
+    if (!out) return fail(LLG_EINVAL, "out is NULL");
+    if (!(b >= 1.0) || n_steps < 1 || !(Tstar0 >= 0.0) || !(h0 >= 0.0) || !(g0 >= 0.0))
+        return fail(LLG_EINVAL, "need b >= 1, n_steps >= 1 and non-negative T*, h, g");
+    llg::gk_flow(Tstar0, h0, g0, b, n_steps, out);
+    return LLG_OK;
+}
+
 llg_status llg_set_axis_dispersion(llg_ctx *c, double half_angle_rad)
 {
     if (!c) return fail(LLG_EINVAL, "ctx is NULL");

@@ -66,6 +66,8 @@ bool derive(int b, double a0, const MaterialIn &m, const ScalingIn &s, const Swe
 // Field (Oe) at step n of a derived sweep (host, FP64).
 double field_Oe(const Derived &d, const SweepIn &w, long long n);
 KParams kparams_of(const Derived &d, int nx, int ny, int nz, unsigned periodic, double dt);
+// Grinstein-Koch flow from l = 0 to ln b: out = {T*, h, g, zeta} (host, FP64).
+void gk_flow(double Ts0, double h0, double g0, double b, long long n_steps, double out[4]);
 
 // ---- plain engine (k_plain.cu): state in global memory, two launches per step --------------
 // m, mt: [n_real][ncells][3]; acc, hth: same shape (scratch).

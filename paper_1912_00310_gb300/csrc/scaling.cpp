@@ -143,6 +143,37 @@ KParams kparams_of(const Derived &d, int nx, int ny, int nz, unsigned periodic, 
     return p;
 }
 
+// Grinstein-Koch flow (Eqs. 4-7) in l = ln b, fourth-order Runge-Kutta with n_steps equal steps;
+// state {T*, h, g, I} with I the running integral of F, zeta = exp(-I).
+void gk_flow(double Ts0, double h0, double g0, double b, long long n_steps, double out[4])
+{
+    struct S {
+        double Ts, h, g, I;
+    };
+    auto rate = [](const S &s) {
+        const double F = s.Ts / (2.0 * kPi * (1.0 + s.h + s.g));
+        return S{(F - 1.0) * s.Ts, 2.0 * s.h, 2.0 * (1.0 - F) * s.g, F};
+    };
+    auto step = [](const S &s, const S &k, double c) {
+        return S{s.Ts + c * k.Ts, s.h + c * k.h, s.g + c * k.g, s.I + c * k.I};
+    };
+    const double dl = std::log(b) / (double)n_steps;
+    S s{Ts0, h0, g0, 0.0};
+    for (long long i = 0; i < n_steps; ++i) {
+        const S k1 = rate(s);
+        const S k2 = rate(step(s, k1, 0.5 * dl));
+        const S k3 = rate(step(s, k2, 0.5 * dl));
+        const S k4 = rate(step(s, k3, dl));
+        const S sum{k1.Ts + 2.0 * (k2.Ts + k3.Ts) + k4.Ts, k1.h + 2.0 * (k2.h + k3.h) + k4.h,
+                    k1.g + 2.0 * (k2.g + k3.g) + k4.g, k1.I + 2.0 * (k2.I + k3.I) + k4.I};
+        s = step(s, sum, dl / 6.0);
+    }
+    out[0] = s.Ts;
+    out[1] = s.h;
+    out[2] = s.g;
+    out[3] = std::exp(-s.I);
+}
+
 double field_Oe(const Derived &d, const SweepIn &w, long long n)
 {
     if (d.shape == 1) {

@@ -129,3 +129,12 @@ def test_loop_stats_match_oracle(pkg, orc):
     f = orc.m_rescale(2, 0.72902, 0.511)
     assert mine["area0_Oe"] == pytest.approx(ref["area"] * f / 0.72902, rel=1e-10)
     assert mine["Hc0_Oe"] == pytest.approx(ref["Hc"] / 0.72902, rel=1e-10)
+
+
+def test_gk_flow_matches_oracle(pkg, orc):
+    for args in ((2 * np.pi * 0.3613, 4.4e-5, 1.8e-5, 22.0), (2.0, 0.05, 0.08, 5.5), (1.0, 0.0, 0.0, 1.0)):
+        mine, ref = pkg.gk_flow(*args), orc.gk_flow(*args)
+        for k in ("Tstar", "h", "g", "zeta"):
+            assert mine[k] == pytest.approx(ref[k], rel=1e-12, abs=1e-300), (args, k)
+    with pytest.raises(pkg.LLGError):
+        pkg.gk_flow(1.0, 0.0, 0.0, 0.5)

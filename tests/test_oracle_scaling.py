@@ -95,3 +95,54 @@ def test_specific_loss_power_formula(orc):
     slp = orc.specific_loss_power(125e3, 480e3, 171.3, 5.17)
     assert slp == pytest.approx(198.8, abs=0.1)
     assert abs(slp - 207.0) / 207.0 < 0.10
+
+
+# ---- the Grinstein-Koch flow (Eqs. 4-7) against its closed forms --------------------------------
+@pytest.mark.parametrize("t", [0.1, 0.3613, 0.6])
+def test_gk_flow_without_field_and_anisotropy_is_the_closed_form(orc, t):
+    """With h = g = 0, F = T*/2pi and the flow integrates in closed form: with u = T*/2pi,
+    du/dl = u (u - 1), so u(l) = 1 / (1 + K e^l), K = (1 - u0)/u0, and
+    zeta = exp(-integral u) = u0 / b + 1 - u0: the analytic zeta of Eq. 11 with t = u0."""
+    for b in (2, 4, 8, 22):
+        r = orc.gk_flow(2 * math.pi * t, 0.0, 0.0, b)
+        assert r["zeta"] == pytest.approx(t / b + 1 - t, rel=1e-12), b
+        K = (1 - t) / t
+        assert r["Tstar"] == pytest.approx(2 * math.pi / (1 + K * b), rel=1e-12), b
+        assert r["h"] == 0.0 and r["g"] == 0.0
+
+
+def test_gk_flow_invariants_give_eqs_8_to_10(orc):
+    """For any h and g: d/dl [T* zeta e^l] = 0, d/dl [g e^(-2l) zeta^(-2)] = 0 and h = h0 e^(2l).
+    With T* = k_B T Lambda / A and Lambda = 2 pi / (b a0) the first gives A(b) = zeta A0 (Eq. 8),
+    the second K(b) = zeta^3 K0 (Eq. 9) and the third H(b) = zeta H0 (Eq. 10)."""
+    T0, h0, g0 = 2 * math.pi * 0.45, 0.05, 0.08
+    for b in (2, 5.5, 22):
+        r = orc.gk_flow(T0, h0, g0, b)
+        assert r["Tstar"] * r["zeta"] * b == pytest.approx(T0, rel=1e-10)
+        assert r["g"] == pytest.approx(g0 * b * b * r["zeta"] ** 2, rel=1e-10)
+        assert r["h"] == pytest.approx(h0 * b * b, rel=1e-10)
+        # the h and g terms lower F, so zeta lies above the h = g = 0 closed form
+        assert r["zeta"] > 0.45 / b + 1 - 0.45
+
+
+def test_gk_flow_for_magnetite_matches_the_printed_zeta(orc):
+    """The paper's claim that for magnetite h and g are so small that the numerical flow is
+    practically indistinguishable from the analytic zeta: with the reading t = T/Tc
+    (T*0 = 2 pi t) and the field at its 500 Oe amplitude, the flow stays within 0.1% of the
+    analytic zeta up to b = 22 (h grows as b^2: 0.021 at b = 22) and within 5e-4 of the four
+    printed values."""
+    M = MAGNETITE
+    red = orc.reduced_parameters(T=M["T"], A=M["A0"], K=M["K0"], Ms=M["Ms"], H_Oe=500.0,
+                                 a=M["a0"])
+    assert red["h"] < 1e-4 and red["g"] < 1e-4
+    t = M["T"] / M["Tc"]
+    g = golden()
+    for b in (2, 4, 8, 22):
+        r = orc.gk_flow(2 * math.pi * t, red["h"], red["g"], b)
+        assert 0 < r["zeta"] / orc.zeta(b, M["T"], M["Tc"]) - 1 < 1e-3, b
+        assert r["zeta"] == pytest.approx(g[f"zeta_{b}"][0], abs=5e-4), b
+    # the physical reduced temperature k_B T Lambda0 / A0 instead corresponds to
+    # t' = k_B T / (a0 A0) = 0.52, which does not give the printed values
+    tp = red["Tstar"] / (2 * math.pi)
+    assert tp == pytest.approx(0.5206, abs=1e-4)
+    assert round(orc.gk_flow(red["Tstar"], red["h"], red["g"], 4)["zeta"], 4) != g["zeta_4"][0]
