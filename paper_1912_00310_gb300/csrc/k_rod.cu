@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_ker
 // ------------------------------------------------------------------------------------------
 // NY, NZ > 0: the rod's y and z extents are compile-time constants (the b = 1 rod), so every
 // shared-memory offset of the stencil is an immediate.
-template <int R, int NX, int NY = 0, int NZ = 0>
+template <int R, int NX, int NY = 0, int NZ = 0, int SHAPE = -1>
 struct PipelinedRod {
     float4 *M, *S;
     int ny_rt, PL_rt, ncell;
@@ -457,7 +457,7 @@ struct PipelinedRod {
         for (int j = 0; j < R; ++j) mA[j] = mB[j] = tA[j] = tB[j] = acc[j] = hth[j] = zero3();
         __syncthreads();
 
-        Sweep field;
+        SweepOf<SHAPE> field;
         field.init(s0, p);
         float Hs = field.value();  // field at step s
         field.inc();
@@ -613,7 +613,7 @@ struct BalancedSchedule {
 
 // balanced == 0: one rod per CTA over [step0, step0 + n_steps).
 // balanced == 1: the segments of `sched`; needs all CTAs co-resident (cooperative launch).
-template <int R, int NX, int NY = 0, int NZ = 0>
+template <int R, int NX, int NY = 0, int NZ = 0, int SHAPE = -1>
 __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_kernel(
     KParams p, float *__restrict__ m_glob, long long step0, int n_steps, float *__restrict__ samples,
     int *__restrict__ status, unsigned *__restrict__ flags, int balanced,
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_
     extern __shared__ float4 sm4[];
     const int PL = (p.nz + 2) * p.ny;
     for (int i = threadIdx.x; i < (NX + 2) * PL; i += blockDim.x) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    PipelinedRod<R, NX, NY, NZ> w;
+    PipelinedRod<R, NX, NY, NZ, SHAPE> w;
     w.setup(sm4, p);
     __syncthreads();
     __shared__ int go;
@@ -658,6 +658,35 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_
 }
 
 int round_warp(int n) { return (n + 31) / 32 * 32; }
+
+// Threads of the plane-pipelined kernel for `rows` rows at up to R rows per thread (thread t owns
+// rows t, t + T, t + 2T, ...).  Every plane ends in a CTA barrier, so a plane takes as long as the
+// busiest of the SM's four schedulers (warp w issues on scheduler w mod 4), whose load is the sum
+// of its warps' row counts.  Among the warp counts that fit the register budget, take the one with
+// the smallest busiest-scheduler load, then the most warps (more latency hiding; no warp without
+// a row).  For the b = 1
+// rod's 1344 rows and R = 3: 16 warps with loads 11/11/10/10 row-warps per scheduler instead of
+// 14 warps with 12/12/9/9.
+int pipelined_threads(int rows, int R)
+{
+    const int wmin = (rows + 32 * R - 1) / (32 * R);
+    const int wmax = std::min(pipelined_max_threads(R) / 32, (rows + 31) / 32);
+    int best_w = wmin, best_load = 1 << 30;
+    for (int w = wmin; w <= wmax; ++w) {
+        const int T = 32 * w;
+        int load[4] = {0, 0, 0, 0};
+        for (int i = 0; i < w; ++i) {
+            const int t = 32 * i;  // a warp's row count is its first thread's
+            load[i & 3] += std::min(R, (rows - t + T - 1) / T);
+        }
+        const int worst = std::max(std::max(load[0], load[1]), std::max(load[2], load[3]));
+        if (worst <= best_load) {
+            best_load = worst;
+            best_w = w;
+        }
+    }
+    return 32 * best_w;
+}
 
 }  // namespace
 
@@ -709,7 +738,7 @@ bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_ki
     if (R < 1 || R > 4 || (rows + R - 1) / R > pipelined_max_threads(R)) return false;
     plan->kind = 2;
     plan->rows_per_thread = R;
-    plan->threads = round_warp((rows + R - 1) / R);
+    plan->threads = pipelined_threads(rows, R);
     plan->rods_per_cta = 1;
     plan->cells_per_thread = 0;
     plan->smem_bytes = pipe_bytes;
@@ -762,7 +791,7 @@ static cudaError_t launch_nx(const KParams &p, const RodPlan &plan, float *m, in
                              long long n_steps, float *samples, int *status, unsigned *flags,
                              cudaStream_t st)
 {
-    auto kern = rod_pipelined_nx_kernel<R, NX, NY, NZ>;
+    auto kern = p.shape == 1 ? rod_pipelined_nx_kernel<R, NX, NY, NZ, 1> : rod_pipelined_nx_kernel<R, NX, NY, NZ, 0>;
     cudaError_t e = set_smem(kern, plan.smem_bytes);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, per_sm = 0;

@@ -191,26 +191,37 @@ __device__ __forceinline__ float3 easy_axis(uint32_t seed, uint32_t real, uint32
 //            (period = 2 n_half; n_half = 0 holds H0);
 //   shape 1: cosine, amp * cos(2 pi ph / period) (the paper's sinusoidal field with its phase
 //            chosen to start at +amp).
-struct Sweep {
-    long long ph, period, n_half;
-    float H0, slope, amp;
+// (a, c) = (H0, slope) for the triangle, (amp, unused) for the cosine; period 0 holds H0.  The
+// triangle coordinate is min(ph, period - ph) since its period is 2 n_half.  SHAPE = 0 or 1 fixes
+// the shape at compile time (the hot resident kernel, whose registers are all in use across the
+// step loop, instantiates one per shape); -1 branches on p.shape.
+template <int SHAPE>
+struct SweepOf {
+    long long ph, period;
+    float a, c;
     int shape;
 
     __host__ __device__ __forceinline__ void init(long long n, const KParams &p)
     {
+        if constexpr (SHAPE == 0) {
+            period = 2 * p.n_half;
+            a = p.H0;
+        } else if constexpr (SHAPE == 1) {
+            period = p.period;
+            a = p.amp;
+        } else {
+            period = p.shape == 1 ? p.period : 2 * p.n_half;
+            a = p.shape == 1 ? p.amp : p.H0;
+        }
         shape = p.shape;
-        n_half = p.n_half;
-        period = p.shape == 1 ? p.period : 2 * p.n_half;
-        H0 = p.H0;
-        slope = p.slope;
-        amp = p.amp;
+        c = p.slope;
         ph = period > 0 ? n % period : 0;
     }
     __device__ __forceinline__ float value() const
     {
-        if (shape == 1) return amp * cospif(2.0f * ((float)ph / (float)period));
-        const long long tri = ph <= n_half ? ph : 2 * n_half - ph;
-        return fmaf(slope, (float)tri, H0);
+        if (SHAPE == 1 || (SHAPE < 0 && shape == 1)) return a * cospif(2.0f * ((float)ph / (float)period));
+        const long long tri = min(ph, period - ph);
+        return fmaf(c, (float)tri, a);
     }
     __host__ __device__ __forceinline__ void inc()
     {
@@ -221,5 +232,6 @@ struct Sweep {
         if (period > 0) ph = (ph == 0 ? period : ph) - 1;
     }
 };
+using Sweep = SweepOf<-1>;
 
 }  // namespace llg
