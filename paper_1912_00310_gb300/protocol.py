@@ -27,7 +27,7 @@ import numpy as np
 from . import ENGINE_AUTO, Grid
 
 MAGNETITE = dict(a0=0.839e-9, A0=0.98e-11, Ms=480e3, K0=10e3, alpha=0.1, T=310.0, Tc=858.0,
-                 delta=0.511)
+                 delta=0.511, rho=5170.0)  # rho: density (kg/m^3) of the specific loss power
 ROD_CELLS = (8, 24, 56)                     # the rod in cells of a0
 BLOCK_B = 22                                # the single-block level
 DT_BY_B = {1: 2e-15, 2: 5e-15, 4: 10e-15, 8: 20e-15, BLOCK_B: 20e-15}
@@ -62,6 +62,13 @@ def make_grid(b: int, *, H_max=500.0, rate=2.5, dt=None, alpha=None, disp_deg=5.
     return g
 
 
+def specific_loss_power_W_per_g(area_Oe: float, f_Hz: float) -> float:
+    """Specific loss power f mu0 (1000 / 4 pi) Ms S / rho of a loop of area S (Oe) at frequency f
+    (the SR/alpha paragraph), in W/g."""
+    mu0 = 4e-7 * math.pi
+    return f_Hz * mu0 * (1000.0 / (4.0 * math.pi)) * MAGNETITE["Ms"] * area_Oe / MAGNETITE["rho"] / 1000.0
+
+
 def run(b: int, n_real: int, seed: int = 0, *, tune=True, paper=PAPER_AREA_OE, **kw) -> dict:
     """One loop per realisation at level b; the loop observables (jackknife standard errors)
     with the rescaled area beside the paper's."""
@@ -80,6 +87,10 @@ def run(b: int, n_real: int, seed: int = 0, *, tune=True, paper=PAPER_AREA_OE, *
         out.update(st)
         out["rate_Oe_per_ns"] = kw.get("rate", 2.5)
         out["alpha"] = MAGNETITE["alpha"] if kw.get("alpha") is None else kw["alpha"]
+        # the loss power at the frequency whose SR, at the run's SR/alpha, has alpha = 0.1
+        rate0 = out["rate_Oe_per_ns"] * MAGNETITE["alpha"] / out["alpha"]
+        out["slp_W_per_g_at_alpha_0p1"] = specific_loss_power_W_per_g(
+            out["area0_Oe"], rate0 * 1e9 / (4.0 * kw.get("H_max", 500.0)))
         out["paper_area0_Oe"] = paper.get(b)
         if out["paper_area0_Oe"]:
             out["area0_over_paper"] = out["area0_Oe"] / out["paper_area0_Oe"]
