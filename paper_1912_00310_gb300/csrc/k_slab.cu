@@ -7,7 +7,9 @@
 // are the lateral neighbours the corrector needs) and the corrector of plane z-1 on the tile,
 // writing the new state straight to the output buffer.  State planes with a two-cell halo are
 // staged by 16-byte asynchronous copies (cp.async) into a ring of three plane buffers, so the
-// load of plane z+2 overlaps the arithmetic of plane z; the predictor planes are double-buffered.
+// load of plane z+2 overlaps the arithmetic of plane z.  Three predictor planes rotate with z, so
+// the corrector re-reads the predictor values of its own cell and of its z- neighbour instead of
+// carrying them in registers (which spilled at four columns per thread).
 // HBM traffic per cell-step: one read of the state (plus the tile halo, mostly served by L2) and
 // one write.  Periodic x and y faces wrap; z faces are free.  The arithmetic, the neighbour order
 // (x-, x+, y-, y+, z-, z+) and the noise keys are those of every other engine, so the trajectory
@@ -62,7 +64,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
     const int pitch = G.TXmax + 4;                 // halo-2 planes
     const int mplane = pitch * (G.TYmax + 4);
     float4 *Mb = sm4;                               // [3][mplane] state planes
-    float4 *Tb = sm4 + 3 * mplane;                  // [2][mplane] predictor planes (same geometry)
+    float4 *Tb = sm4 + 3 * mplane;                  // [3][mplane] predictor planes (same geometry)
                                                     // then the staging table (int2 per position)
     const bool perx = p.periodic & 1u, pery = p.periodic & 2u;
     const size_t plane_cells = (size_t)G.NX * G.NY;
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
     // Staging table of this tile, built once: for every halo-2 position (smem offset in a plane,
     // offset of its cell in a global plane or -1 outside a free face).  Each plane load is then a
     // table read and a 16-byte asynchronous copy per position.
-    int2 *desc = reinterpret_cast<int2 *>(Tb + 2 * mplane);
+    int2 *desc = reinterpret_cast<int2 *>(Tb + 3 * mplane);
     const int w = TX + 4, h = TY + 4, npos = w * h;
     for (int i = threadIdx.x; i < npos; i += blockDim.x) {
         const int lx = i % w - 2, ly = i / w - 2;
@@ -114,14 +116,16 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
         pos[k] = (ly + 2) * pitch + (lx + 2);
         cell[k] = (uint32_t)((x0 + lx) + G.NX * (y0 + ly));  // + NX*NY*z per plane
     }
-    // the ring cell of this thread (predictor only)
+    // the ring cell of this thread (predictor only), counted from the last thread down: the last
+    // threads own the fewest interior columns
     const int nring = 2 * (TX + 2) + 2 * TY;
-    const bool ract = threadIdx.x < nring;
+    const int ridx = (int)blockDim.x - 1 - (int)threadIdx.x;
+    const bool ract = ridx < nring;
     int rpos = 0;
     uint32_t rcell = 0;
     bool rin = false;
     {
-        const int i = ract ? threadIdx.x : 0;
+        const int i = ract ? ridx : 0;
         int lx, ly;
         if (i < 2 * (TX + 2)) {
             lx = i % (TX + 2) - 1;
@@ -137,9 +141,12 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
         rcell = (uint32_t)(gx + G.NX * gy);
     }
 
-    float3 mA[CPT], mB[CPT], tA[CPT], tB[CPT], acc[CPT], hth[CPT];
+    // per column: the state at z-1 and z for the predictor, the corrector's accumulator and
+    // thermal field one plane behind; the predictor values of planes z-2 and z-1 the corrector
+    // needs are re-read from the three predictor slots (fewer registers than carrying them)
+    float3 mA[CPT], mB[CPT], acc[CPT], hth[CPT];
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) mA[k] = mB[k] = tA[k] = tB[k] = acc[k] = hth[k] = zero3s();
+    for (int k = 0; k < CPT; ++k) mA[k] = mB[k] = acc[k] = hth[k] = zero3s();
     float3 rA = zero3s(), rB = zero3s();
 
     load_plane(0, 0);
@@ -162,7 +169,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
         if (z < G.NZ) {
             const float4 *Mz = Mb + (z % 3) * mplane;
             const float4 *Mn = Mb + ((z + 1) % 3) * mplane;
-            float4 *Tw = Tb + (z & 1) * mplane;
+            float4 *Tw = Tb + (z % 3) * mplane;
             const bool has_next = z + 1 < G.NZ;
             const uint32_t zoff = (uint32_t)(plane_cells * (size_t)z);
 #pragma unroll
@@ -207,7 +214,8 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
         }
         if (z > 0) {
             const int zc = z - 1;
-            const float4 *Tr = Tb + (zc & 1) * mplane;
+            const float4 *Tr = Tb + (zc % 3) * mplane;
+            const float4 *Tp = Tb + ((zc + 2) % 3) * mplane;  // plane zc - 1 (read only when zc > 0)
             const bool has_next = z < G.NZ;
             float4 *out = dst + plane_cells * (size_t)zc;
 #pragma unroll
@@ -215,22 +223,22 @@ __global__ void __launch_bounds__(kSlabThreads, 1) slab_step_kernel(KParams p, S
                 if (!act[k]) continue;
                 const int t = pos[k];
                 const float3 tnext = has_next ? tnew[k] : zero3s();
+                const float3 tprev = zc > 0 ? xyz(Tp[t]) : zero3s();
+                const float3 tself = xyz(Tr[t]);
                 float3 nb = add3(xyz(Tr[t - 1]), xyz(Tr[t + 1]));
                 nb = add3(nb, xyz(Tr[t - pitch]));
                 nb = add3(nb, xyz(Tr[t + pitch]));
-                nb = add3(nb, tA[k]);
+                nb = add3(nb, tprev);
                 nb = add3(nb, tnext);
                 const float3 u = AX ? xyz(__ldg(axr + cell[k] + plane_cells * (size_t)zc)) : zero3s();
-                const float3 H = effective_field_sel<AX>(nb, tB[k], hth[k], p, Hn1, u);
-                const float3 s1 = llg_torque(tB[k], H, p.alpha);
+                const float3 H = effective_field_sel<AX>(nb, tself, hth[k], p, Hn1, u);
+                const float3 s1 = llg_torque(tself, H, p.alpha);
                 out[cell[k]] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[k])));
             }
         }
         if (z < G.NZ) {
 #pragma unroll
             for (int k = 0; k < CPT; ++k) {
-                tA[k] = z == 0 ? zero3s() : tB[k];
-                tB[k] = tnew[k];
                 acc[k] = anew[k];
                 hth[k] = hnew[k];
             }
@@ -314,17 +322,20 @@ bool slab_plan(const KParams &p, int dev, SlabPlan *plan)
     // keep the columns per thread within the compiled variants and the shared memory within
     // the opt-in limit
     auto smem_of = [&](int ty) {
-        return (size_t)5 * (TXmax + 4) * (ty + 4) * sizeof(float4) + (size_t)(TXmax + 4) * (ty + 4) * sizeof(int2);
+        return (size_t)6 * (TXmax + 4) * (ty + 4) * sizeof(float4) + (size_t)(TXmax + 4) * (ty + 4) * sizeof(int2);
     };
     while (TYmax > 1 && (TXmax * TYmax > 4 * kSlabThreads || smem_of(TYmax) > (size_t)smem_optin)) {
         ++tiles_y;
         TYmax = (p.ny + tiles_y - 1) / tiles_y;
     }
     if (TXmax * TYmax > 4 * kSlabThreads || smem_of(TYmax) > (size_t)smem_optin) return false;
+    // All kSlabThreads threads once a tile has more columns than that (more warps at the same
+    // register budget; the last threads, with one column fewer, take the predictor ring).
     const int cols = TXmax * TYmax;
     const int cpt = (cols + kSlabThreads - 1) / kSlabThreads;
-    const int threads = std::max(32, (std::max((cols + cpt - 1) / cpt, 2 * (TXmax + 2) + 2 * TYmax) + 31) / 32 * 32);
-    if (threads > kSlabThreads) return false;
+    const int ring = 2 * (TXmax + 2) + 2 * TYmax;
+    const int threads = std::min(kSlabThreads, std::max(32, (std::max(cols, ring) + 31) / 32 * 32));
+    if (ring > threads) return false;
     plan->tiles_x = tiles_x;
     plan->tiles_y = tiles_y;
     plan->TXmax = TXmax;
