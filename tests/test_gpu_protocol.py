@@ -321,3 +321,32 @@ def test_dispersion_adjoint_matches_oracle_gradient(pkg, orc):
     for k in range(3):
         assert grad[k] == pytest.approx(go[k], rel=1e-2, abs=1e-3 * np.abs(go).max()), (k, grad, go)
     g.close()
+
+
+def test_protocol_runner_matches_oracle_statistics(pkg, orc):
+    """The paper-protocol runner end to end at b = 8 (sinusoid, 5-degree dispersion, delta
+    rescaling, autotuned launch) on a fast cycle: +-500 Oe at 250 Oe/ns with alpha = 1, 64
+    realisations.  Its rescaled area and coercive field against the oracle's loops of the same
+    realisations, within 3 combined standard errors."""
+    from paper_1912_00310_gb300 import protocol as P
+    n_real, kw = 64, dict(H_max=500.0, rate=250.0, alpha=1.0, sample_dH=5.0)
+    r = P.run(8, n_real, seed=4, **kw)
+    assert r["steps"] == 400000 and r["b"] == 8
+    dims, _ = P.level_grid(8)
+    p = orc.material_problem(*dims, a0=M["a0"], b=8, A0=M["A0"], K0=M["K0"], Ms=M["Ms"], alpha=1.0,
+                             T=M["T"], dt=P.DT_BY_B[8], mode=2, Tc=M["Tc"], H_start_Oe=500.0,
+                             rate_Oe_per_ns=250.0, shape=1, disp=math.radians(5.0))
+    every = orc.sample_interval(5.0, 250.0, P.DT_BY_B[8])
+    ns = p.period // every + 1
+    ref = orc.uniform_state(n_real, p.ncells)
+    s, _ = orc.run(p, ref, seed=4, n_steps=p.period, sample_every=every, n_samples=ns)
+    s[:, 0] = 1.0
+    H = np.array([orc.field_Oe(p, k * every) for k in range(ns)])
+    o = orc.loop_stats(H, s, (ns - 1) // 2)
+    f = orc.m_rescale(2, r["zeta"], M["delta"]) / r["zeta"]
+    se = math.hypot(o["area_se"], r["area_se_Oe"])
+    assert abs(o["area"] - r["area_Oe"]) <= 3 * se, (o["area"], r["area_Oe"], se)
+    assert r["area0_Oe"] == pytest.approx(r["area_Oe"] * f, rel=1e-9)
+    se = math.hypot(o["Hc_se"], r["Hc_se_Oe"])
+    assert abs(o["Hc"] - r["Hc_Oe"]) <= 3 * se, (o["Hc"], r["Hc_Oe"], se)
+    assert r["slp_W_per_g_at_alpha_0p1"] > 0

@@ -146,3 +146,17 @@ def test_gk_flow_for_magnetite_matches_the_printed_zeta(orc):
     tp = red["Tstar"] / (2 * math.pi)
     assert tp == pytest.approx(0.5206, abs=1e-4)
     assert round(orc.gk_flow(red["Tstar"], red["h"], red["g"], 4)["zeta"], 4) != g["zeta_4"][0]
+
+
+def test_protocol_levels_and_loss_power():
+    """The protocol runner's host-side pieces: the rod cut at each level (the printed cell counts),
+    the b = 22 block's volume, and the specific loss power formula on the printed S = 171.3 Oe."""
+    from paper_1912_00310_gb300 import protocol as P
+    assert P.level_grid(1) == ((8, 24, 56), 0.0)
+    assert P.level_grid(2)[0] == (4, 12, 28) and P.level_grid(8)[0] == (1, 3, 7)
+    dims, V = P.level_grid(22)
+    assert dims == (1, 1, 1) and V == pytest.approx(10752 * MAGNETITE["a0"] ** 3, rel=1e-12)
+    with pytest.raises(ValueError):
+        P.level_grid(3)
+    # f mu0 (1000/4pi) Ms S / rho at 125 kHz: 198.8 W/g for the printed area (R13)
+    assert P.specific_loss_power_W_per_g(171.3, 125e3) == pytest.approx(198.8, abs=0.05)
