@@ -168,6 +168,11 @@ llg_status llg_set_engine(llg_ctx *ctx, int engine);
  *                             specialised for the plane count exists
  *   LLG_TUNE_BALANCE          0: one rod per CTA even when the rods do not fill whole waves
  *                             (default 1: rod-steps balanced over a co-resident grid)
+ *   LLG_TUNE_ADJOINT_STATE_MB device memory (MB, default 16384) that llg_loop_area_grad may hold
+ *                             for the whole window's states (12 bytes per cell, realisation and
+ *                             step); within it every checkpoint segment is recomputed in one
+ *                             launch and the window reversed in another, beyond it (or with 0)
+ *                             segment by segment.  The gradient is the same either way.
  * The arithmetic, and so the trajectory, does not depend on these.  Errors: EINVAL (unknown
  * key, negative value); EUNSUPPORTED at the next advance if the shape cannot hold the grid. */
 #define LLG_TUNE_ROD_KIND 1
@@ -176,6 +181,7 @@ llg_status llg_set_engine(llg_ctx *ctx, int engine);
 #define LLG_TUNE_ROWS_PER_THREAD 4
 #define LLG_TUNE_GENERIC_KERNEL 5
 #define LLG_TUNE_BALANCE 6
+#define LLG_TUNE_ADJOINT_STATE_MB 7
 llg_status llg_set_tuning(llg_ctx *ctx, int key, int64_t value);
 
 /* ---------------------------------------------------------------------------------------- */

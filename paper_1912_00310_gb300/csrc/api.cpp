@@ -33,6 +33,7 @@ struct llg_ctx {
     double ax_disp = 0.0;
     int engine = LLG_ENGINE_AUTO;
     int tune_kind = 0, tune_rods = 0, tune_rows = 0, tune_generic = 0, tune_balance = 1;
+    long long adjoint_state_mb = 16384;  // budget for the adjoint's stored window states
     long long chunk_steps = 1LL << 20;
     // ensemble
     int n_real = 0;
@@ -444,6 +445,10 @@ llg_status llg_set_tuning(llg_ctx *c, int key, int64_t value)
         case LLG_TUNE_BALANCE:
             c->tune_balance = value != 0;
             return LLG_OK;
+        case LLG_TUNE_ADJOINT_STATE_MB:
+            if (value > (1LL << 22)) return fail(LLG_EINVAL, "at most 4 TB for the adjoint's states");
+            c->adjoint_state_mb = value;
+            return LLG_OK;
         case LLG_TUNE_CHUNK_STEPS:
             if (value > (1LL << 30)) return fail(LLG_EINVAL, "at most 2^30 steps per launch");
             c->chunk_steps = value > 0 ? value : (1LL << 20);
@@ -667,6 +672,18 @@ llg_status llg_loop_area_grad(llg_ctx *c, int64_t n_steps, int objective, const 
     if (k_last >= d.n_samples && d.n_half > 0) return fail(LLG_EINVAL, "the window runs past the end of the loop");
     const size_t state = (size_t)c->n_real * (size_t)ncells_of(c) * 3;
     const long long ns_total = std::max<long long>(d.n_samples, k_last + 1);
+    // store the whole window's states when they fit the budget and a quarter of the free memory
+    bool store_all = false;
+    {
+        const double bytes = (double)sizeof(float) * (double)state * (double)N;
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            cudaGetLastError();
+            free_b = 0;
+        }
+        store_all = S <= 65535 && N <= 0x7fffffffLL && bytes <= (double)c->adjoint_state_mb * 1048576.0 &&
+                    bytes <= 0.25 * (double)free_b;
+    }
     float *ckpt = nullptr, *seg = nullptr, *lam = nullptr, *work = nullptr, *smp = nullptr;
     double *w = nullptr, *partial = nullptr;
     auto cleanup = [&]() {
@@ -679,7 +696,7 @@ llg_status llg_loop_area_grad(llg_ctx *c, int64_t n_steps, int objective, const 
         cudaFree(partial);
     };
     cudaError_t e = cudaMalloc(&ckpt, sizeof(float) * state * (size_t)S);
-    if (e == cudaSuccess) e = cudaMalloc(&seg, sizeof(float) * state * (size_t)std::min(C, N));
+    if (e == cudaSuccess) e = cudaMalloc(&seg, sizeof(float) * state * (size_t)(store_all ? N : std::min(C, N)));
     if (e == cudaSuccess) e = cudaMalloc(&lam, sizeof(float) * state);
     if (e == cudaSuccess) e = cudaMalloc(&work, sizeof(float) * state);
     if (e == cudaSuccess) e = cudaMalloc(&smp, sizeof(float) * (size_t)c->n_real * (size_t)ns_total);
@@ -736,10 +753,16 @@ llg_status llg_loop_area_grad(llg_ctx *c, int64_t n_steps, int objective, const 
     e = cudaMemcpyAsync(w, wk.data(), sizeof(double) * (size_t)K, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(lam, 0, sizeof(float) * state, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(partial, 0, sizeof(double) * 5 * (size_t)c->n_real, st);
-    for (long long sg = S - 1; sg >= 0 && e == cudaSuccess; --sg) {
-        const long long len = std::min(C, N - sg * C);
-        e = llg::adjoint_segment(kps, c->n_real, step0 + sg * C, (int)len, step0 + N, k_first, (int)K,
-                                 ckpt + (size_t)sg * state, seg, lam, w, partial, st);
+    if (store_all) {
+        if (e == cudaSuccess) e = llg::adjoint_recompute_all(kps, c->n_real, step0, N, (int)C, ckpt, seg, st);
+        if (e == cudaSuccess)
+            e = llg::adjoint_backward_all(kps, c->n_real, step0, N, k_first, (int)K, seg, lam, w, partial, st);
+    } else {
+        for (long long sg = S - 1; sg >= 0 && e == cudaSuccess; --sg) {
+            const long long len = std::min(C, N - sg * C);
+            e = llg::adjoint_segment(kps, c->n_real, step0 + sg * C, (int)len, step0 + N, k_first, (int)K,
+                                     ckpt + (size_t)sg * state, seg, lam, w, partial, st);
+        }
     }
     std::vector<double> hp((size_t)c->n_real * 5);
     if (e == cudaSuccess)

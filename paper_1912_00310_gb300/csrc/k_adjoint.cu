@@ -20,11 +20,14 @@
 // and dL/dm of the previous state is g_m.  The host maps (g_alpha, g_a, g_cex, g_can, g_sigma)
 // to the scale factors (g_sigma is accumulated as g_H.h_th, i.e. sigma dL/dsigma).
 //
-// One CTA per rod, one cell per thread, the rod in shared memory with a zero ghost layer.  A
-// launch handles one checkpoint segment: it first recomputes the segment's states forward from
-// the checkpoint (bitwise the forward run: same arithmetic), storing them in global scratch
-// (L2-resident for the calibration workload), then walks them backward.  Parameter partial sums
-// are FP64 per thread and per CTA.
+// One CTA per rod, one cell per thread, the rod in shared memory with a zero ghost layer.  The
+// kernel has two phases: recompute the states of a checkpoint segment forward from its checkpoint
+// (bitwise the forward run: same arithmetic) into global memory, and walk stored states backward.
+// With memory to spare (the whole window's states, 12 bytes per cell, realisation and step), one
+// launch recomputes every segment at once (a CTA per rod and segment) and one launch walks the
+// whole window back, so the recomputation leaves the sequential critical path; otherwise each
+// segment is recomputed and reversed in turn in one launch.  Parameter partial sums are FP64 per
+// thread and per CTA.
 #include <cmath>
 
 #include "llg_internal.h"
@@ -50,6 +53,10 @@ struct AdjParams {
     long long k_first;    // sample number of w[0]
     int n_k;
     float inj_scale;      // 1 / (n_real * ncells)
+    int phases;           // bit 0: recompute the segment forward; bit 1: walk it backward
+    int seg_stride;       // recompute with gridDim.y > 1: segment blockIdx.y starts seg_stride
+                          // steps after seg_start (its checkpoint and states offset to match)
+    long long n_total;    // ... and the window has n_total steps (the last segment is shorter)
 };
 
 // Neighbour sum over the six faces (x-, x+, y-, y+, z-, z+) of a ghost-padded rod.
@@ -87,8 +94,18 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
     const size_t state = (size_t)ncell * 3;
     const size_t rod_off = (size_t)rod * state;
     const int n_rods = gridDim.x;
+    long long seg_start = ap.seg_start;
+    int seg_len = ap.seg_len;
+    if (gridDim.y > 1) {  // one segment of a window recomputed all at once
+        const long long off = (long long)blockIdx.y * ap.seg_stride;
+        seg_start += off;
+        seg_len = (int)min((long long)ap.seg_stride, ap.n_total - off);
+        ckpt += (size_t)blockIdx.y * n_rods * state;
+        seg += (size_t)off * n_rods * state;
+    }
     float3 m = zero3a();
-    if (act) m = make_float3(ckpt[rod_off + 3 * c], ckpt[rod_off + 3 * c + 1], ckpt[rod_off + 3 * c + 2]);
+    if (act && (ap.phases & 1))
+        m = make_float3(ckpt[rod_off + 3 * c], ckpt[rod_off + 3 * c + 1], ckpt[rod_off + 3 * c + 2]);
     float3 u = make_float3(0.f, 0.f, 1.f);  // easy axis (dispersed-axis mode, AX)
     if (AX && act) u = xyz(__ldg(p.axis + (size_t)rod * ncell + c));
     auto field_of = [&](float3 nb, float3 mm, float3 hh, float Hz) {
@@ -98,10 +115,10 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
 
     // ---- forward recomputation of the segment: seg[j] = state before step seg_start + j ----
     Sweep field;
-    field.init(ap.seg_start, p);
+    field.init(seg_start, p);
     float Hn = field.value();
-    for (int j = 0; j < ap.seg_len; ++j) {
-        const unsigned long long n = (unsigned long long)(ap.seg_start + j);
+    for (int j = 0; j < ((ap.phases & 1) ? seg_len : 0); ++j) {
+        const unsigned long long n = (unsigned long long)(seg_start + j);
         field.inc();
         const float Hn1 = field.value();
         float *sj = seg + (size_t)j * n_rods * state + rod_off;
@@ -130,6 +147,7 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
         Hn = Hn1;
     }
 
+    if (!(ap.phases & 2)) return;
     // ---- backward through the segment ----
     float3 g = zero3a();  // dL/d(state after the step being reversed)
     if (act) g = make_float3(lam[rod_off + 3 * c], lam[rod_off + 3 * c + 1], lam[rod_off + 3 * c + 2]);
@@ -137,9 +155,9 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
     const float a = -p.neg_dt_g1;  // dt g1
     const float ha = -p.neg_hdt_g1;
     const float alpha = p.alpha;
-    field.init(ap.seg_start + ap.seg_len - 1, p);
-    for (int j = ap.seg_len - 1; j >= 0; --j) {
-        const long long n = ap.seg_start + j;
+    field.init(seg_start + seg_len - 1, p);
+    for (int j = seg_len - 1; j >= 0; --j) {
+        const long long n = seg_start + j;
         const float hn = field.value();
         Sweep f1 = field;
         f1.inc();
@@ -266,9 +284,29 @@ bool adjoint_supported(const KParams &p, int dev)
     return p.periodic == 0 && p.ncells <= 1024 && 4 * rod_pad * sizeof(float4) <= (size_t)smem_optin;
 }
 
-cudaError_t adjoint_segment(const KParams &p, int n_real, long long seg_start, int seg_len, long long win_end,
-                            long long k_first, int n_k, const float *ckpt, float *seg, float *lam,
-                            const double *w, double *partial, cudaStream_t st)
+namespace {
+cudaError_t launch_adjoint(const AdjParams &ap, int n_real, int n_seg, const float *ckpt, float *seg, float *lam,
+                           const double *w, double *partial, cudaStream_t st)
+{
+    const KParams &p = ap.p;
+    const size_t rod_pad = (size_t)(p.nx + 2) * (p.ny + 2) * (p.nz + 2);
+    const size_t smem = 4 * rod_pad * sizeof(float4);
+    const int threads = (p.ncells + 31) / 32 * 32;
+    const dim3 grid((unsigned)n_real, (unsigned)n_seg);
+    if (p.axis) {
+        cudaError_t e = cudaFuncSetAttribute(adjoint_segment_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        adjoint_segment_kernel<true><<<grid, threads, smem, st>>>(ap, ckpt, seg, lam, w, partial);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(adjoint_segment_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        adjoint_segment_kernel<false><<<grid, threads, smem, st>>>(ap, ckpt, seg, lam, w, partial);
+    }
+    return cudaGetLastError();
+}
+
+AdjParams adj_params(const KParams &p, int n_real, long long seg_start, int seg_len, long long win_end,
+                     long long k_first, int n_k, int phases)
 {
     AdjParams ap;
     ap.p = p;
@@ -278,19 +316,39 @@ cudaError_t adjoint_segment(const KParams &p, int n_real, long long seg_start, i
     ap.k_first = k_first;
     ap.n_k = n_k;
     ap.inj_scale = 1.0f / ((float)n_real * (float)p.ncells);
-    const size_t rod_pad = (size_t)(p.nx + 2) * (p.ny + 2) * (p.nz + 2);
-    const size_t smem = 4 * rod_pad * sizeof(float4);
-    const int threads = (p.ncells + 31) / 32 * 32;
-    if (p.axis) {
-        cudaError_t e = cudaFuncSetAttribute(adjoint_segment_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        adjoint_segment_kernel<true><<<n_real, threads, smem, st>>>(ap, ckpt, seg, lam, w, partial);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(adjoint_segment_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        adjoint_segment_kernel<false><<<n_real, threads, smem, st>>>(ap, ckpt, seg, lam, w, partial);
-    }
-    return cudaGetLastError();
+    ap.phases = phases;
+    ap.seg_stride = 0;
+    ap.n_total = 0;
+    return ap;
+}
+}  // namespace
+
+cudaError_t adjoint_segment(const KParams &p, int n_real, long long seg_start, int seg_len, long long win_end,
+                            long long k_first, int n_k, const float *ckpt, float *seg, float *lam,
+                            const double *w, double *partial, cudaStream_t st)
+{
+    const AdjParams ap = adj_params(p, n_real, seg_start, seg_len, win_end, k_first, n_k, 3);
+    return launch_adjoint(ap, n_real, 1, ckpt, seg, lam, w, partial, st);
+}
+
+cudaError_t adjoint_recompute_all(const KParams &p, int n_real, long long step0, long long n_steps, int ckpt_every,
+                                  const float *ckpt, float *states, cudaStream_t st)
+{
+    const long long n_seg = (n_steps + ckpt_every - 1) / ckpt_every;
+    if (n_seg < 1 || n_seg > 65535) return cudaErrorInvalidValue;
+    AdjParams ap = adj_params(p, n_real, step0, ckpt_every, step0 + n_steps, 0, 0, 1);
+    ap.seg_stride = ckpt_every;
+    ap.n_total = n_steps;
+    return launch_adjoint(ap, n_real, (int)n_seg, ckpt, states, nullptr, nullptr, nullptr, st);
+}
+
+cudaError_t adjoint_backward_all(const KParams &p, int n_real, long long step0, long long n_steps, long long k_first,
+                                 int n_k, const float *states, float *lam, const double *w, double *partial,
+                                 cudaStream_t st)
+{
+    if (n_steps < 1 || n_steps > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const AdjParams ap = adj_params(p, n_real, step0, (int)n_steps, step0 + n_steps, k_first, n_k, 2);
+    return launch_adjoint(ap, n_real, 1, nullptr, const_cast<float *>(states), lam, w, partial, st);
 }
 
 }  // namespace llg

@@ -134,6 +134,14 @@ bool adjoint_supported(const KParams &p, int dev);
 cudaError_t adjoint_segment(const KParams &p, int n_real, long long seg_start, int seg_len, long long win_end,
                             long long k_first, int n_k, const float *ckpt, float *seg, float *lam,
                             const double *w, double *partial, cudaStream_t st);
+// The same reverse pass with the whole window's states stored: states[j] (j < n_steps, each
+// n_real * ncells * 3 floats) = the state before step step0 + j, recomputed for all checkpoint
+// segments in one launch (ckpt: one state per ckpt_every steps), then walked back in one launch.
+cudaError_t adjoint_recompute_all(const KParams &p, int n_real, long long step0, long long n_steps, int ckpt_every,
+                                  const float *ckpt, float *states, cudaStream_t st);
+cudaError_t adjoint_backward_all(const KParams &p, int n_real, long long step0, long long n_steps, long long k_first,
+                                 int n_k, const float *states, float *lam, const double *w, double *partial,
+                                 cudaStream_t st);
 
 // ---- host runtime helpers (api.cpp) ---------------------------------------------------------
 // Store a message for llg_last_error() on this thread.

@@ -119,3 +119,23 @@ def test_calibration_workload_launch_shape(pkg):
     assert float(loss) == pytest.approx(L, rel=1e-12)
     assert np.allclose(s.grad.numpy(), grad, rtol=1e-12)
     g.close()
+
+
+@pytest.mark.parametrize("ckpt_every,disp", [(512, 0.0), (300, 0.3)])
+def test_stored_window_equals_segment_by_segment(pkg, ckpt_every, disp):
+    """The two reverse schedules (every segment recomputed at once into a stored window, or one
+    segment at a time) compute the same arithmetic: bitwise-equal loss and gradient, with a ragged
+    last segment and in the dispersed-axis mode."""
+    dims, n_real, n_steps = ROD_DIMS[4], 6, 2000
+    out = []
+    for budget in (16384, 0):
+        g = grid(pkg, dims)
+        g.set_axis_dispersion(disp)
+        g.set_tuning(pkg.TUNE_ADJOINT_STATE_MB, budget)
+        g.reset(seed=9, n_real=n_real)
+        g.advance(150)
+        out.append(g.loss_grad(n_steps, target_for(g), 0, ckpt_every))
+        assert g.step == 150
+        g.close()
+    assert out[0][0] == out[1][0]
+    assert list(out[0][1]) == list(out[1][1])
