@@ -69,8 +69,10 @@ __device__ __forceinline__ float3 nsum(const float4 *A, int q, int sy, int sz)
     return add3(nb, xyz(A[q + sz]));
 }
 
-template <bool AX>
-__global__ void __launch_bounds__(1024) adjoint_segment_kernel(
+// MAXT: the largest CTA the instance runs with (256 for rods up to 256 cells, which then get up to
+// 255 registers per thread, 1024 otherwise).
+template <bool AX, int MAXT>
+__global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
     AdjParams ap, const float *__restrict__ ckpt, float *__restrict__ seg, float *__restrict__ lam,
     const double *__restrict__ w, double *__restrict__ partial)
 {
@@ -156,6 +158,13 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
     const float ha = -p.neg_hdt_g1;
     const float alpha = p.alpha;
     field.init(seg_start + seg_len - 1, p);
+    // the stored state of the next step to reverse, loaded one step ahead (a stored window is
+    // larger than L2, so each load would otherwise wait on HBM)
+    float3 m_ahead = zero3a();
+    if (act && seg_len > 0) {
+        const float *sl = seg + (size_t)(seg_len - 1) * n_rods * state + rod_off;
+        m_ahead = make_float3(sl[3 * c], sl[3 * c + 1], sl[3 * c + 2]);
+    }
     for (int j = seg_len - 1; j >= 0; --j) {
         const long long n = seg_start + j;
         const float hn = field.value();
@@ -168,11 +177,14 @@ __global__ void __launch_bounds__(1024) adjoint_segment_kernel(
             const long long k = done / p.sample_every - ap.k_first;
             if (k >= 0 && k < ap.n_k) g.z += (float)w[k] * ap.inj_scale;
         }
-        const float *sj = seg + (size_t)j * n_rods * state + rod_off;
         float3 mi = zero3a(), h = zero3a(), H = zero3a(), c0 = zero3a(), s0 = zero3a(), t = zero3a();
         float pn = 1.f;
         if (act) {
-            mi = make_float3(sj[3 * c], sj[3 * c + 1], sj[3 * c + 2]);
+            mi = m_ahead;
+            if (j > 0) {
+                const float *sn = seg + (size_t)(j - 1) * n_rods * state + rod_off;
+                m_ahead = make_float3(sn[3 * c], sn[3 * c + 1], sn[3 * c + 2]);
+            }
             M[q] = pad4(mi);
         }
         __syncthreads();
@@ -293,16 +305,15 @@ cudaError_t launch_adjoint(const AdjParams &ap, int n_real, int n_seg, const flo
     const size_t smem = 4 * rod_pad * sizeof(float4);
     const int threads = (p.ncells + 31) / 32 * 32;
     const dim3 grid((unsigned)n_real, (unsigned)n_seg);
-    if (p.axis) {
-        cudaError_t e = cudaFuncSetAttribute(adjoint_segment_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto go = [&](auto kern) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        adjoint_segment_kernel<true><<<grid, threads, smem, st>>>(ap, ckpt, seg, lam, w, partial);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(adjoint_segment_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        adjoint_segment_kernel<false><<<grid, threads, smem, st>>>(ap, ckpt, seg, lam, w, partial);
-    }
-    return cudaGetLastError();
+        kern<<<grid, threads, smem, st>>>(ap, ckpt, seg, lam, w, partial);
+        return cudaGetLastError();
+    };
+    if (threads <= 256)
+        return p.axis ? go(adjoint_segment_kernel<true, 256>) : go(adjoint_segment_kernel<false, 256>);
+    return p.axis ? go(adjoint_segment_kernel<true, 1024>) : go(adjoint_segment_kernel<false, 1024>);
 }
 
 AdjParams adj_params(const KParams &p, int n_real, long long seg_start, int seg_len, long long win_end,
