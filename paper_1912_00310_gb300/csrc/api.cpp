@@ -696,7 +696,12 @@ llg_status llg_loop_area_grad(llg_ctx *c, int64_t n_steps, int objective, const 
         cudaFree(partial);
     };
     cudaError_t e = cudaMalloc(&ckpt, sizeof(float) * state * (size_t)S);
-    if (e == cudaSuccess) e = cudaMalloc(&seg, sizeof(float) * state * (size_t)(store_all ? N : std::min(C, N)));
+    if (e == cudaSuccess && store_all && cudaMalloc(&seg, sizeof(float) * state * (size_t)N) != cudaSuccess) {
+        cudaGetLastError();  // no room for the whole window: reverse segment by segment
+        seg = nullptr;
+        store_all = false;
+    }
+    if (e == cudaSuccess && !store_all) e = cudaMalloc(&seg, sizeof(float) * state * (size_t)std::min(C, N));
     if (e == cudaSuccess) e = cudaMalloc(&lam, sizeof(float) * state);
     if (e == cudaSuccess) e = cudaMalloc(&work, sizeof(float) * state);
     if (e == cudaSuccess) e = cudaMalloc(&smp, sizeof(float) * (size_t)c->n_real * (size_t)ns_total);
