@@ -158,13 +158,17 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
     const float ha = -p.neg_hdt_g1;
     const float alpha = p.alpha;
     field.init(seg_start + seg_len - 1, p);
-    // the stored state of the next step to reverse, loaded one step ahead (a stored window is
-    // larger than L2, so each load would otherwise wait on HBM)
-    float3 m_ahead = zero3a();
+    // Three barriers per reversed step.  The state before step j sits in M from the previous
+    // iteration (it is stored there with the last shared write of that iteration, after every
+    // read of M), and the stored state of the next step to reverse is loaded one step ahead (a
+    // stored window is larger than L2, so each load would otherwise wait on HBM).
+    float3 m_cur = zero3a(), m_ahead = zero3a();
     if (act && seg_len > 0) {
         const float *sl = seg + (size_t)(seg_len - 1) * n_rods * state + rod_off;
-        m_ahead = make_float3(sl[3 * c], sl[3 * c + 1], sl[3 * c + 2]);
+        m_cur = make_float3(sl[3 * c], sl[3 * c + 1], sl[3 * c + 2]);
+        M[q] = pad4(m_cur);
     }
+    __syncthreads();
     for (int j = seg_len - 1; j >= 0; --j) {
         const long long n = seg_start + j;
         const float hn = field.value();
@@ -180,14 +184,12 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
         float3 mi = zero3a(), h = zero3a(), H = zero3a(), c0 = zero3a(), s0 = zero3a(), t = zero3a();
         float pn = 1.f;
         if (act) {
-            mi = m_ahead;
+            mi = m_cur;
             if (j > 0) {
                 const float *sn = seg + (size_t)(j - 1) * n_rods * state + rod_off;
                 m_ahead = make_float3(sn[3 * c], sn[3 * c + 1], sn[3 * c + 2]);
             }
-            M[q] = pad4(mi);
         }
-        __syncthreads();
         float3 Nm = zero3a();
         if (act) {
             h = thermal_field(p.seed, real, (uint32_t)c, (unsigned long long)n, p.sigma);
@@ -243,6 +245,7 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
             gH = cross3(gc0, mi);
             g_alpha += (double)dot3(cross3(mi, c0), gs0);
             GH[q] = pad4(gH);
+            if (j > 0) M[q] = pad4(m_ahead);  // M was last read before the previous barrier
         }
         __syncthreads();
         if (act) {
@@ -258,8 +261,10 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
             g_cex += (double)dot3(gH, Nm);
             g_sigma += (double)dot3(gH, h);
             g = gm;
+            m_cur = m_ahead;
         }
-        __syncthreads();
+        // no barrier here: the next iteration's first shared write (P) follows reads of P that
+        // ended before this iteration's second barrier, and GH is next written after two barriers
         // step back the field phase
         field.dec();
     }
