@@ -483,6 +483,7 @@ llg_status llg_reset(llg_ctx *c, uint32_t seed, int n_real, uint32_t real_offset
 
 llg_status llg_advance(llg_ctx *c, int64_t n_steps, float *m_samples)
 {
+    llg::NvtxRange nvtx("llg_advance");
     if (!c) return fail(LLG_EINVAL, "ctx is NULL");
     if (c->n_real < 1 || !c->d_m) return fail(LLG_EINVAL, "no ensemble (llg_reset first)");
     if (n_steps < 0) return fail(LLG_EINVAL, "n_steps must be >= 0");
@@ -565,6 +566,7 @@ llg_status llg_sync(llg_ctx *c, double timeout_s)
 llg_status llg_run_loops(llg_ctx *c, uint32_t seed, int n_real, uint32_t real_offset, float *m_samples,
                          llg_loop_stats *stats)
 {
+    llg::NvtxRange nvtx("llg_run_loops");
     if (!c) return fail(LLG_EINVAL, "ctx is NULL");
     if (!m_samples) return fail(LLG_EINVAL, "m_samples is required");
     llg::Derived d;
@@ -644,6 +646,7 @@ llg_status llg_set_state(llg_ctx *c, const float *m, int64_t step)
 llg_status llg_loop_area_grad(llg_ctx *c, int64_t n_steps, int objective, const double *target,
                               int64_t ckpt_every, double *loss_out, double grad_out[3])
 {
+    llg::NvtxRange nvtx("llg_loop_area_grad");
     if (!c) return fail(LLG_EINVAL, "ctx is NULL");
     if (c->n_real < 1 || !c->d_m) return fail(LLG_EINVAL, "no ensemble (llg_reset first)");
     if (n_steps < 1 || ckpt_every < 1 || ckpt_every > (1 << 20)) return fail(LLG_EINVAL, "need n_steps >= 1, 1 <= ckpt_every <= 2^20");

@@ -47,6 +47,7 @@ std::map<TuneKey, TuneValue> g_tune_cache;
 
 extern "C" llg_status llg_autotune(llg_ctx *ctx, int64_t trial_steps, double *best_rate)
 {
+    llg::NvtxRange nvtx("llg_autotune");
     if (!ctx || trial_steps < 1) {
         llg::set_last_error("need a context and trial_steps >= 1");
         return LLG_EINVAL;
@@ -138,6 +139,7 @@ extern "C" llg_status llg_autotune(llg_ctx *ctx, int64_t trial_steps, double *be
 extern "C" llg_status llg_run_batch(llg_ctx *const *jobs, int n_jobs, int64_t max_steps,
                                     float *const *m_samples, int64_t *steps_done)
 {
+    llg::NvtxRange nvtx("llg_run_batch");
     if (!jobs || n_jobs < 1 || max_steps < 0) {
         llg::set_last_error("need jobs, n_jobs >= 1, max_steps >= 0");
         return LLG_EINVAL;

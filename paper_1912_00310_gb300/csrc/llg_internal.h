@@ -3,11 +3,21 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/llg.h"
 
 namespace llg {
+
+// NVTX range around one C-ABI call (header-only NVTX3: no cost unless a profiler is attached), so
+// that timelines and ncu ranges show which call issued which launches.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Simulation-level coefficients of one job, derived on the host in FP64 (scaling.cpp).
 struct Derived {
