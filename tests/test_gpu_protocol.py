@@ -350,3 +350,23 @@ def test_protocol_runner_matches_oracle_statistics(pkg, orc):
     se = math.hypot(o["Hc_se"], r["Hc_se_Oe"])
     assert abs(o["Hc"] - r["Hc_Oe"]) <= 3 * se, (o["Hc"], r["Hc_Oe"], se)
     assert r["slp_W_per_g_at_alpha_0p1"] > 0
+
+
+@pytest.mark.parametrize("dims,rods,disp", [((10, 10, 10), 1, 0.3), ((12, 12, 12), 1, 0.3),
+                                            ((12, 12, 12), 1, 0.0), (ROD_DIMS[4], 3, 0.3)])
+def test_twophase_variants_bitwise_with_plain(pkg, dims, rods, disp):
+    """The two-phase kernel with two and four cells per thread (1000- and 1728-cell grids) and with
+    three rods per CTA, under the sinusoid, with and without dispersed axes: bitwise equal to the
+    plain engine."""
+    n_real, outs = 5, []
+    for eng, kind in ((pkg.ENGINE_RESIDENT, 1), (pkg.ENGINE_PLAIN, 0)):
+        g = sine_grid(pkg, dims, 4, engine=eng, kind=kind)
+        if rods > 1:
+            g.set_tuning(pkg.TUNE_RODS_PER_CTA, rods)
+        g.set_axis_dispersion(disp)
+        g.reset(seed=12, n_real=n_real)
+        g.advance(60)
+        outs.append(state_of(g, n_real))
+        g.close()
+    assert torch.equal(outs[0], outs[1])
+    assert float((torch.linalg.norm(outs[0], dim=-1) - 1).abs().max()) < 1e-6
