@@ -1,5 +1,6 @@
 // scaling.cpp -- host FP64 parameter setup of one job: the coarse-graining map (Eqs. 8-13), the
-// coefficients of Eq. 1 and of the Brown thermal field, and the triangle field sweep.
+// coefficients of Eq. 1 and of the Brown thermal field, the triangle and sinusoidal field sweeps and
+// the numerical Grinstein-Koch flow (Eqs. 4-7).
 #include <cmath>
 #include <cstdio>
 
