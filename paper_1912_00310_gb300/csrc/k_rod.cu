@@ -18,6 +18,15 @@
 //      the last plane of step n shares its iteration with the predictor of plane 0 of step n+1,
 //      so every iteration does both halves of the work: nx barriers per step.
 //
+//  rod_pipelined_nx_kernel: the same schedule with the plane count (and, for the b = 1 rod, the
+//      whole shape) and the sweep shape fixed at compile time, unrolled over the planes and run
+//      over a co-resident grid with a balanced schedule of rod-steps (McNaughton's wrap-around
+//      rule) when the rods do not fill whole waves.
+//
+// The thread count of the plane-pipelined kernels balances the rows over the SM's four
+// schedulers (pipelined_threads).  The dispersed-axis mode (per-cell easy axes in global memory)
+// runs the AX instances of the two-phase and runtime-size plane-pipelined kernels.
+//
 // Both kernels add the neighbours in the order x-, x+, y-, y+, z-, z+ with exact zeros for
 // missing ones and use the same physics.cuh arithmetic as the plain engine, so all engines
 // produce bitwise-identical trajectories.  Samples use the canonical warp reduction (reduce.cuh).

@@ -1,6 +1,7 @@
 // physics.cuh -- device arithmetic of one stochastic Heun step of Eq. 1 (FP32), shared by every
-// engine of the library: the Philox4x32-10 noise source, the Box-Muller thermal normals, the LLG
-// torque and the renormalisation.
+// engine of the library: the Philox4x32-10 noise source, the Box-Muller thermal normals, the
+// effective field (easy axis z or a per-cell axis), the LLG torque, the renormalisation and the
+// field sweep (triangle or sinusoid) evaluated from an integer phase.
 //
 // Eq. 1 for the unit vector m = M/Ms:  dm/dt = -g1 m x H - alpha g1 m x (m x H),
 // g1 = mu0 ge / (1 + alpha^2).  Writing s(m, H) = m x H + alpha m x (m x H), the right-hand side
