@@ -111,6 +111,7 @@ def main(argv=None):
     ap.add_argument("--h-max", type=float, default=500.0)
     ap.add_argument("--alpha", type=float, default=None)
     ap.add_argument("--disp-deg", type=float, default=5.0)
+    ap.add_argument("--dt", type=float, default=None, help="time step (s); default by level b")
     a = ap.parse_args(argv)
     pairs = [(a.rate, a.alpha)]
     paper = PAPER_AREA_OE
@@ -122,7 +123,7 @@ def main(argv=None):
     for b in a.b:
         for rate, alpha in pairs:
             r = run(b, a.n_real, a.seed, paper=paper, H_max=a.h_max, rate=rate, alpha=alpha,
-                    disp_deg=a.disp_deg)
+                    disp_deg=a.disp_deg, dt=a.dt)
             print(json.dumps(r), flush=True)
 
 
