@@ -7,11 +7,11 @@ import pytest
 from workloads import MAGNETITE as M, random_unit_state
 
 
-def _setup(orc, dims=(1, 2, 3), n_real=16, disp=0.0):
+def _setup(orc, dims=(1, 2, 3), n_real=16, disp=0.0, shape=0):
     p = orc.material_problem(*dims, a0=M["a0"], b=4, A0=M["A0"], K0=M["K0"], Ms=M["Ms"],
                              alpha=M["alpha"], T=M["T"], dt=10e-15, mode=1, Tc=M["Tc"],
                              H_start_Oe=1500.0, H_turn_Oe=-1500.0, rate_Oe_per_ns=1000.0,
-                             disp=disp)
+                             disp=disp, shape=shape)
     m0 = np.ascontiguousarray(random_unit_state(n_real, p.ncells, seed=21, cone=0.6))
     n_samples = 2 * p.n_half // 100 + 1
     target = 0.92 + 0.05 * np.cos(np.arange(n_samples) / 7.0)
@@ -28,10 +28,11 @@ def _loss(orc, p, m0, target, scale, step0, n_steps, every):
     return float(np.mean((mbar - target[k_first:k_last + 1]) ** 2)), mbar
 
 
-@pytest.mark.parametrize("scale,disp", [((1.0, 1.0, 1.0), 0.0), ((1.3, 0.7, 1.15), 0.0),
-                                        ((1.1, 0.9, 1.05), 0.0872664626)])
-def test_gradient_matches_central_differences(orc, scale, disp):
-    p, m0, target = _setup(orc, disp=disp)
+@pytest.mark.parametrize("scale,disp,shape", [((1.0, 1.0, 1.0), 0.0, 0), ((1.3, 0.7, 1.15), 0.0, 0),
+                                              ((1.1, 0.9, 1.05), 0.0872664626, 0),
+                                              ((0.9, 1.2, 0.95), 0.0872664626, 1)])
+def test_gradient_matches_central_differences(orc, scale, disp, shape):
+    p, m0, target = _setup(orc, disp=disp, shape=shape)
     step0, n_steps, every = 300, 2000, 100
     L, g, mbar = orc.loss_grad(p, m0, target=target, scale=scale, seed=3, step0=step0,
                                n_steps=n_steps, sample_every=every)
