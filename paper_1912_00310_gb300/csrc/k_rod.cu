@@ -25,7 +25,8 @@
 //
 // The thread count of the plane-pipelined kernels balances the rows over the SM's four
 // schedulers (pipelined_threads).  The dispersed-axis mode (per-cell easy axes in global memory)
-// runs the AX instances of the two-phase and runtime-size plane-pipelined kernels.
+// runs the AX instances: of the two-phase kernel, of the runtime-size plane-pipelined kernel and,
+// for the b = 1 rod at three rows per thread, of the shape-specialised one.
 //
 // Both kernels add the neighbours in the order x-, x+, y-, y+, z-, z+ with exact zeros for
 // missing ones and use the same physics.cuh arithmetic as the plain engine, so all engines
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_ker
 // ------------------------------------------------------------------------------------------
 // NY, NZ > 0: the rod's y and z extents are compile-time constants (the b = 1 rod), so every
 // shared-memory offset of the stencil is an immediate.
-template <int R, int NX, int NY = 0, int NZ = 0, int SHAPE = -1>
+template <int R, int NX, int NY = 0, int NZ = 0, int SHAPE = -1, bool AX = false>
 struct PipelinedRod {
     float4 *M, *S;
     int ny_rt, PL_rt, ncell;
@@ -459,6 +460,7 @@ struct PipelinedRod {
                                                              __ldcg(g + 3 * (size_t)c + 2), 0.f);
         }
         const PhiloxKeys keys = philox_keys(p.seed, p.real0 + (uint32_t)rod);
+        const float4 *axr = AX ? p.axis + (size_t)rod * ncell : nullptr;  // easy axes (AX)
         // carried per row: m(x-1), m(x) for the predictor; m~(x-2), m~(x-1), acc(x-1), h(x-1)
         // for the corrector one plane behind
         float3 mA[R], mB[R], tA[R], tB[R], acc[R], hth[R];
@@ -478,6 +480,14 @@ struct PipelinedRod {
         float3 hpre[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) hpre[j] = thermal_field(keys, cbase[j], (unsigned long long)s0, p.sigma);
+        // AX: the easy axis of the next predictor's cell, loaded one iteration ahead like the
+        // noise, and the axis of the plane the corrector works on (the previous predictor's)
+        float3 upre[R], ucor[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            upre[j] = ucor[j] = zero3();
+            if constexpr (AX) upre[j] = xyz(__ldg(axr + cbase[j]));
+        }
 
         for (long long s = 0; s < ns; ++s) {
             const unsigned long long n = (unsigned long long)(s0 + s);
@@ -502,7 +512,7 @@ struct PipelinedRod {
                     nb = axpy(wp[j], xyz(Mp[qq + 1]), nb);
                     nb = add3(nb, xyz(Mp[qq - ny]));
                     nb = add3(nb, xyz(Mp[qq + ny]));
-                    const float3 H = effective_field(nb, mB[j], hnew[j], p.c_ex, p.c_an, Hs);
+                    const float3 H = effective_field_sel<AX>(nb, mB[j], hnew[j], p, Hs, upre[j]);
                     const float3 s0v = llg_torque(mB[j], H, p.alpha);
                     tnew[j] = normalised(axpy(p.neg_dt_g1, s0v, mB[j]));
                     anew[j] = axpy(p.neg_hdt_g1, s0v, mB[j]);
@@ -526,7 +536,7 @@ struct PipelinedRod {
                         nb = axpy(wp[j], xyz(Sr[qq + 1]), nb);
                         nb = add3(nb, xyz(Sr[qq - ny]));
                         nb = add3(nb, xyz(Sr[qq + ny]));
-                        const float3 H = effective_field(nb, tB[j], hth[j], p.c_ex, p.c_an, Hc);
+                        const float3 H = effective_field_sel<AX>(nb, tB[j], hth[j], p, Hc, ucor[j]);
                         const float3 s1 = llg_torque(tB[j], H, p.alpha);
                         Mw[qq] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[j])));
                     }
@@ -540,6 +550,10 @@ struct PipelinedRod {
                     // the next predictor: plane x+1 of this step, or plane 0 of the next one
                     hpre[j] = x + 1 < NX ? thermal_field(keys, cbase[j] + (uint32_t)(x + 1), n, p.sigma)
                                          : thermal_field(keys, cbase[j], n + 1, p.sigma);
+                    if constexpr (AX) {
+                        ucor[j] = upre[j];
+                        upre[j] = xyz(__ldg(axr + cbase[j] + (uint32_t)(x + 1 < NX ? x + 1 : 0)));
+                    }
                 }
                 __syncthreads();
                 if (x == 0 && s > 0 && s0 + s == next_sample) {
@@ -565,7 +579,7 @@ struct PipelinedRod {
                 nb = axpy(wp[j], xyz(Sr[qq + 1]), nb);
                 nb = add3(nb, xyz(Sr[qq - ny]));
                 nb = add3(nb, xyz(Sr[qq + ny]));
-                const float3 H = effective_field(nb, tB[j], hth[j], p.c_ex, p.c_an, Hprev);
+                const float3 H = effective_field_sel<AX>(nb, tB[j], hth[j], p, Hprev, ucor[j]);
                 const float3 s1 = llg_torque(tB[j], H, p.alpha);
                 Mw[qq] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[j])));
             }
@@ -622,7 +636,7 @@ struct BalancedSchedule {
 
 // balanced == 0: one rod per CTA over [step0, step0 + n_steps).
 // balanced == 1: the segments of `sched`; needs all CTAs co-resident (cooperative launch).
-template <int R, int NX, int NY = 0, int NZ = 0, int SHAPE = -1>
+template <int R, int NX, int NY = 0, int NZ = 0, int SHAPE = -1, bool AX = false>
 __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_kernel(
     KParams p, float *__restrict__ m_glob, long long step0, int n_steps, float *__restrict__ samples,
     int *__restrict__ status, unsigned *__restrict__ flags, int balanced,
@@ -632,7 +646,7 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_
     extern __shared__ float4 sm4[];
     const int PL = (p.nz + 2) * p.ny;
     for (int i = threadIdx.x; i < (NX + 2) * PL; i += blockDim.x) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    PipelinedRod<R, NX, NY, NZ, SHAPE> w;
+    PipelinedRod<R, NX, NY, NZ, SHAPE, AX> w;
     w.setup(sm4, p);
     __syncthreads();
     __shared__ int go;
@@ -795,12 +809,12 @@ static void balanced_schedule(int n_real, int N, int G, BalancedSchedule *sc)
 
 // Launch of the nx-specialised kernel: balanced over a co-resident grid when the rods do not
 // divide evenly into waves, else one rod per CTA.
-template <int R, int NX, int NY = 0, int NZ = 0>
+template <int R, int NX, int NY = 0, int NZ = 0, bool AX = false>
 static cudaError_t launch_nx(const KParams &p, const RodPlan &plan, float *m, int n_real, long long step0,
                              long long n_steps, float *samples, int *status, unsigned *flags,
                              cudaStream_t st)
 {
-    auto kern = p.shape == 1 ? rod_pipelined_nx_kernel<R, NX, NY, NZ, 1> : rod_pipelined_nx_kernel<R, NX, NY, NZ, 0>;
+    auto kern = p.shape == 1 ? rod_pipelined_nx_kernel<R, NX, NY, NZ, 1, AX> : rod_pipelined_nx_kernel<R, NX, NY, NZ, 0, AX>;
     cudaError_t e = set_smem(kern, plan.smem_bytes);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, per_sm = 0;
@@ -854,6 +868,11 @@ cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_r
                 return cudaErrorInvalidValue;
         }
 #undef LLG_TWOPHASE
+    } else if (plan.kind == 2 && p.axis && plan.rows_per_thread == 3 && p.nx == 8 && p.ny == 24 && p.nz == 56 &&
+               !plan.generic) {
+        // the b = 1 rod with dispersed axes: the shape-specialised kernel's axis instance
+        e = launch_nx<3, 8, 24, 56, true>(p, plan, m, n_real, step0, n_steps, samples, status, flags, st);
+        if (e != cudaSuccess) return e;
     } else if (plan.kind == 2) {
 #define LLG_PIPELINED(R)                                                                        \
     case R:                                                                                     \

@@ -91,15 +91,17 @@ def test_sinusoid_engines_bitwise_and_oracle(pkg, orc):
         assert torch.equal(s, states[0])
 
 
-def test_sinusoid_b1_rod_specialised_kernel(pkg, orc):
-    """The b = 1 rod runs the shape-specialised plane-pipelined kernel (cosine variant); 160 rods
-    take the balanced schedule.  Bitwise equal to the generic kernel and the plain engine; the last
-    realisation against the oracle."""
+@pytest.mark.parametrize("disp", [0.0, math.radians(5.0)])
+def test_sinusoid_b1_rod_specialised_kernel(pkg, orc, disp):
+    """The b = 1 rod runs the shape-specialised plane-pipelined kernel (cosine variant, and its
+    dispersed-axis instance); 160 rods take the balanced schedule.  Bitwise equal to the generic
+    kernel and the plain engine; the last realisation against the oracle."""
     dims, n_real, steps = ROD_DIMS[1], 160, 300
     kw = dict(dt=2e-15, rate=1e5, H_start=40.0, sample_dH=2.0)  # 0.2 Oe/step, a cycle of 800 steps
     outs = []
     for eng, generic in ((pkg.ENGINE_RESIDENT, 0), (pkg.ENGINE_RESIDENT, 1), (pkg.ENGINE_PLAIN, 0)):
         g = sine_grid(pkg, dims, 1, engine=eng, **kw)
+        g.set_axis_dispersion(disp)
         if generic:
             g.set_tuning(pkg.TUNE_GENERIC_KERNEL, 1)
         g.reset(seed=2, n_real=n_real)
@@ -108,6 +110,7 @@ def test_sinusoid_b1_rod_specialised_kernel(pkg, orc):
         g.close()
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
     p = sine_problem(orc, dims, 1, dt=2e-15, rate=1e5, H_start=40.0)
+    p.disp = disp
     ref = orc.uniform_state(1, p.ncells)
     orc.run(p, ref, seed=2, real0=n_real - 1, n_steps=steps)
     assert float(np.max(np.abs(outs[0][-1].double().cpu().numpy() - ref[0]))) <= 1e-4
