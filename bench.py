@@ -88,7 +88,10 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+        # raw samples: a temporary file, or LLG_BENCH_CLOCKS_DIR to keep them
+        import tempfile
+        out_dir = os.environ.get("LLG_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"llg_bench_clocks_gpu{index}.csv")
 
     def start(self):
         try:
