@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    ap.add_argument("--ladder-full", choices=["ci", "all"], default=None,
+                    help="run every job of the uneven ladder to the end of its loop in batched "
+                         "graph calls and print one JSON line (ci: without the b = 1 jobs at "
+                         "10 Oe/ns); not part of the default benchmark")
     ap.add_argument("--profile-case", default=None,
                     help="run a small untimed case for a profiler (b1, b1-plain, b4) and exit")
     return ap.parse_args()
@@ -474,6 +478,57 @@ def ladder_batch(args, torch, pkg, flush):
             "launch": "one CUDA graph per call (one kernel node per job, longest first)"}
 
 
+def ladder_full(which):
+    """Every job of the uneven ladder (b x rate x alpha, 64 realisations each) run to the end of
+    its loop through the batching layer: graph calls of up to 2e6 Heun steps per job until every
+    loop is complete.  'ci' leaves out the b = 1 jobs at 10 Oe/ns (3e8 steps per loop)."""
+    import time
+    import torch
+    import paper_1912_00310_gb300 as pkg
+    from workloads import CONFIGS, DT_BY_B, MAGNETITE as M, ROD_DIMS
+    c3 = CONFIGS["ladder_batch"]
+    jobs = []
+    for b in c3["bs"]:
+        for rate in c3["rates"]:
+            if which == "ci" and b == 1 and rate == 10.0:
+                continue
+            for alpha in c3["alphas"]:
+                g = pkg.Grid(*ROD_DIMS[b], a0=M["a0"], b=b)
+                g.set_material(A0=M["A0"], Ms=M["Ms"], K0=M["K0"], alpha=alpha, T=M["T"])
+                g.set_scaling(mode=c3["mode"], Tc=M["Tc"])
+                g.set_sweep(H_start=c3["H_start"], H_turn=c3["H_turn"], rate=rate, dt=DT_BY_B[b],
+                            sample_dH=c3["sample_dH"])
+                g.set_engine(pkg.ENGINE_RESIDENT)
+                g.reset(seed=c3["seed"], n_real=c3["n_real"], real_offset=len(jobs) * c3["n_real"])
+                g.autotune(trial_steps=100)
+                g.reset(seed=c3["seed"], n_real=c3["n_real"], real_offset=len(jobs) * c3["n_real"])
+                jobs.append(g)
+    samples = [torch.zeros((c3["n_real"], g.n_samples), device="cuda") for g in jobs]
+    for S in samples:
+        S[:, 0] = 1.0
+    cell_steps = sum(c3["n_real"] * g.ncells * g.steps_per_loop for g in jobs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    calls = 0
+    while True:
+        done = pkg.run_batch(jobs, 2_000_000, samples)
+        calls += 1
+        if not any(done):
+            break
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    finished = all(g.step == g.steps_per_loop for g in jobs)
+    loops = len(jobs) * c3["n_real"]
+    finite = all(bool(torch.isfinite(S).all()) for S in samples)
+    for g in jobs:
+        g.close()
+    print(json.dumps({"leg": "ladder_full", "variant": which, "jobs": len(jobs), "loops": loops,
+                      "all_loops_complete": finished, "samples_finite": finite,
+                      "cell_steps": cell_steps, "seconds": sec, "graph_calls": calls,
+                      "loops_per_s": loops / sec, "cell_steps_per_s": cell_steps / sec,
+                      "unit": UNIT}), flush=True)
+
+
 def slab_stream(args, torch, pkg, flush):
     """The 512x512x56 periodic slab with the streaming engine: one fused Heun step per launch."""
     from workloads import CONFIGS
@@ -582,6 +637,8 @@ def main():
     args = parse()
     if args.profile_case:
         return profile_case(args.profile_case)
+    if args.ladder_full:
+        return ladder_full(args.ladder_full)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
