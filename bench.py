@@ -515,6 +515,10 @@ def ladder_full(which):
         calls += 1
         if not any(done):
             break
+        torch.cuda.synchronize()
+        left = sum(1 for g in jobs if g.step < g.steps_per_loop)
+        print(f"ladder_full: call {calls}, {time.perf_counter() - t0:.1f} s, {left} of {len(jobs)} "
+              f"jobs unfinished", file=sys.stderr, flush=True)
     torch.cuda.synchronize()
     sec = time.perf_counter() - t0
     finished = all(g.step == g.steps_per_loop for g in jobs)
