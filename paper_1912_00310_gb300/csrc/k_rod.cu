@@ -685,26 +685,30 @@ int round_warp(int n) { return (n + 31) / 32 * 32; }
 // Threads of the plane-pipelined kernel for `rows` rows at up to R rows per thread (thread t owns
 // rows t, t + T, t + 2T, ...).  Every plane ends in a CTA barrier, so a plane takes as long as the
 // busiest of the SM's four schedulers (warp w issues on scheduler w mod 4), whose load is the sum
-// of its warps' row counts.  Among the warp counts that fit the register budget, take the one with
-// the smallest busiest-scheduler load, then the most warps (more latency hiding; no warp without
-// a row).  For the b = 1
-// rod's 1344 rows and R = 3: 16 warps with loads 11/11/10/10 row-warps per scheduler instead of
-// 14 warps with 12/12/9/9.
+// of its warps' row counts.  Among the warp counts that fit the register budget (and leave no
+// warp without a row), take the one with the smallest busiest-scheduler load, then the fewest row
+// slots without a row (each still draws its noise, the draw being outside the row branch), then
+// the most warps.  For the b = 1 rod's 1344 rows and R = 3: 15 warps with loads 11/11/11/9
+// row-warps per scheduler and 3 idle row slots, instead of 14 warps at 12/12/9/9 (or 16 warps at
+// 11/11/10/10 with 6 idle slots).
 int pipelined_threads(int rows, int R)
 {
     const int wmin = (rows + 32 * R - 1) / (32 * R);
     const int wmax = std::min(pipelined_max_threads(R) / 32, (rows + 31) / 32);
-    int best_w = wmin, best_load = 1 << 30;
+    int best_w = wmin, best_load = 1 << 30, best_idle = 1 << 30;
     for (int w = wmin; w <= wmax; ++w) {
         const int T = 32 * w;
-        int load[4] = {0, 0, 0, 0};
+        int load[4] = {0, 0, 0, 0}, idle = 0;
         for (int i = 0; i < w; ++i) {
             const int t = 32 * i;  // a warp's row count is its first thread's
-            load[i & 3] += std::min(R, (rows - t + T - 1) / T);
+            const int rows_w = std::min(R, (rows - t + T - 1) / T);
+            load[i & 3] += rows_w;
+            idle += R - rows_w;  // row slots that still draw noise without a row
         }
         const int worst = std::max(std::max(load[0], load[1]), std::max(load[2], load[3]));
-        if (worst <= best_load) {
+        if (worst < best_load || (worst == best_load && idle <= best_idle)) {
             best_load = worst;
+            best_idle = idle;
             best_w = w;
         }
     }
