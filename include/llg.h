@@ -173,7 +173,8 @@ llg_status llg_set_engine(llg_ctx *ctx, int engine);
  *                             step); within it every checkpoint segment is recomputed in one
  *                             launch and the window reversed in another, beyond it (or with 0)
  *                             segment by segment.  The states, and so the loss, are the same
- *                             either way; the gradient's FP64 sums differ in order only.
+ *                             either way; the gradient's partial sums are grouped differently
+ *                             (to about 1e-7 relative).
  * The arithmetic, and so the trajectory, does not depend on these.  Errors: EINVAL (unknown
  * key, negative value); EUNSUPPORTED at the next advance if the shape cannot hold the grid. */
 #define LLG_TUNE_ROD_KIND 1

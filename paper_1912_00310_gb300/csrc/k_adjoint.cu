@@ -45,6 +45,8 @@ __device__ __forceinline__ float3 scale3(float s, float3 a) { return make_float3
 __device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ float3 zero3a() { return make_float3(0.f, 0.f, 0.f); }
 
+constexpr long long kAdjBlock = 64;  // steps per FP32 block of the parameter partial sums
+
 struct AdjParams {
     KParams p;
     long long seg_start;  // first step of the segment
@@ -153,7 +155,20 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
     // ---- backward through the segment ----
     float3 g = zero3a();  // dL/d(state after the step being reversed)
     if (act) g = make_float3(lam[rod_off + 3 * c], lam[rod_off + 3 * c + 1], lam[rod_off + 3 * c + 2]);
+    // parameter partial sums: FP32 within blocks of kAdjBlock steps (aligned to absolute step
+    // numbers, so both reverse schedules form the same block sums), FP64 across blocks -- the
+    // GPU's FP64 rate is a small fraction of its FP32 rate, and a per-step FP64 update made the
+    // reverse step wait on it
     double g_alpha = 0.0, g_a = 0.0, g_cex = 0.0, g_can = 0.0, g_sigma = 0.0;
+    float f_alpha = 0.f, f_a = 0.f, f_cex = 0.f, f_can = 0.f, f_sigma = 0.f;
+    auto flush = [&]() {
+        g_alpha += (double)f_alpha;
+        g_a += (double)f_a;
+        g_cex += (double)f_cex;
+        g_can += (double)f_can;
+        g_sigma += (double)f_sigma;
+        f_alpha = f_a = f_cex = f_can = f_sigma = 0.f;
+    };
     const float a = -p.neg_dt_g1;  // dt g1
     const float ha = -p.neg_hdt_g1;
     const float alpha = p.alpha;
@@ -215,11 +230,11 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
             const float3 mp = scale3(1.f / qn, qv);
             gq = scale3(1.f / qn, sub3(g, scale3(dot3(mp, g), mp)));
             const float3 gs1 = scale3(-ha, gq);
-            g_a += -0.5 * (double)dot3(add3(s0, s1), gq);
+            f_a -= 0.5f * dot3(add3(s0, s1), gq);
             const float3 gc1 = add3(gs1, scale3(alpha, cross3(gs1, t)));
             gmt = add3(scale3(alpha, cross3(c1, gs1)), cross3(Ht, gc1));
             gHt = cross3(gc1, t);
-            g_alpha += (double)dot3(cross3(t, c1), gs1);
+            f_alpha += dot3(cross3(t, c1), gs1);
             GT[q] = pad4(gHt);
         }
         __syncthreads();
@@ -229,21 +244,21 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
             if constexpr (AX) {
                 const float gu = dot3(gHt, u);
                 gmt = axpy(p.c_an * gu, u, gmt);
-                g_can += (double)gu * (double)dot3(t, u);
+                f_can += gu * dot3(t, u);
             } else {
                 gmt.z = fmaf(p.c_an, gHt.z, gmt.z);
-                g_can += (double)gHt.z * (double)t.z;
+                f_can += gHt.z * t.z;
             }
-            g_cex += (double)dot3(gHt, Nt);
-            g_sigma += (double)dot3(gHt, h);  // d/dsigma = (1/sigma) g_H.h, divided on the host
+            f_cex += dot3(gHt, Nt);
+            f_sigma += dot3(gHt, h);  // d/dsigma = (1/sigma) g_H.h, divided on the host
             const float3 gp = scale3(1.f / pn, sub3(gmt, scale3(dot3(t, gmt), t)));
             gm = add3(gq, gp);                                     // q = m - ..., p = m - a s0
             const float3 gs0 = add3(scale3(-ha, gq), scale3(-a, gp));  // from q and from p
-            g_a += -(double)dot3(s0, gp);
+            f_a -= dot3(s0, gp);
             const float3 gc0 = add3(gs0, scale3(alpha, cross3(gs0, mi)));
             gm = add3(gm, add3(scale3(alpha, cross3(c0, gs0)), cross3(H, gc0)));
             gH = cross3(gc0, mi);
-            g_alpha += (double)dot3(cross3(mi, c0), gs0);
+            f_alpha += dot3(cross3(mi, c0), gs0);
             GH[q] = pad4(gH);
             if (j > 0) M[q] = pad4(m_ahead);  // M was last read before the previous barrier
         }
@@ -253,21 +268,23 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
             if constexpr (AX) {
                 const float gu = dot3(gH, u);
                 gm = axpy(p.c_an * gu, u, gm);
-                g_can += (double)gu * (double)dot3(mi, u);
+                f_can += gu * dot3(mi, u);
             } else {
                 gm.z = fmaf(p.c_an, gH.z, gm.z);
-                g_can += (double)gH.z * (double)mi.z;
+                f_can += gH.z * mi.z;
             }
-            g_cex += (double)dot3(gH, Nm);
-            g_sigma += (double)dot3(gH, h);
+            f_cex += dot3(gH, Nm);
+            f_sigma += dot3(gH, h);
             g = gm;
             m_cur = m_ahead;
+            if (n % kAdjBlock == 0) flush();
         }
         // no barrier here: the next iteration's first shared write (P) follows reads of P that
         // ended before this iteration's second barrier, and GH is next written after two barriers
         // step back the field phase
         field.dec();
     }
+    flush();
     if (act) {
         lam[rod_off + 3 * c] = g.x;
         lam[rod_off + 3 * c + 1] = g.y;

@@ -125,8 +125,9 @@ def test_calibration_workload_launch_shape(pkg):
 def test_stored_window_equals_segment_by_segment(pkg, ckpt_every, disp):
     """The two reverse schedules (every segment recomputed at once into a stored window, or one
     segment at a time) compute the same FP32 states: bitwise-equal loss, and gradients that differ
-    only by the order of the FP64 parameter sums (one sum over the window against one per
-    segment), with a ragged last segment and in the dispersed-axis mode."""
+    only by how the parameter partial sums are grouped (FP32 blocks of 64 steps that a segment
+    boundary splits, FP64 across blocks), with a ragged last segment and in the dispersed-axis
+    mode."""
     dims, n_real, n_steps = ROD_DIMS[4], 6, 2000
     out = []
     for budget in (16384, 0):
@@ -139,4 +140,4 @@ def test_stored_window_equals_segment_by_segment(pkg, ckpt_every, disp):
         assert g.step == 150
         g.close()
     assert out[0][0] == out[1][0]
-    assert np.allclose(out[0][1], out[1][1], rtol=1e-12, atol=0)
+    assert np.allclose(out[0][1], out[1][1], rtol=1e-5, atol=0)
