@@ -36,6 +36,8 @@ MAX_SM_MHZ = 2070.0
 # arithmetic: Philox4x32-10 98, uniforms 12, Box-Muller 20, two effective fields 40, two torques
 # 30, predictor with renormalisation and accumulator 12, corrector with renormalisation 9).
 ALU_OPS_PER_CELL_STEP = 221
+# measured FP32 lane issue rate (lane-ops/s) of this run's GPU, set by run_ours
+ALU_PEAK = {"value": None}
 
 
 def parse():
@@ -168,28 +170,42 @@ def timed_steps(torch, fn, K, W, flush):
     return times
 
 
-def cpu_oracle_rate(cfg, budget_s=12.0):
-    """The FP64 oracle on the host cores on a bounded sample of the workload: rods of the same
-    size, a short window of Heun steps.  Returns (cell-steps/s, threads, description)."""
+def _oracle_problem(cfg):
     from oracle import oracle as O
     from workloads import MAGNETITE as M
     O.build()
-    threads = os.cpu_count() or 1
-    p = O.material_problem(*cfg["dims"], a0=M["a0"], b=cfg["b"], A0=M["A0"], K0=M["K0"],
-                           Ms=M["Ms"], alpha=M["alpha"], T=M["T"], dt=cfg["dt"], mode=cfg["mode"],
-                           Tc=M["Tc"], H_start_Oe=cfg["H_start"], H_turn_Oe=cfg["H_turn"],
-                           rate_Oe_per_ns=cfg["rate"])
-    n_real = threads
-    # calibrate on a short run, then size the measured run to the budget
+    return O, O.material_problem(*cfg["dims"], a0=M["a0"], b=cfg["b"], A0=M["A0"], K0=M["K0"],
+                                 Ms=M["Ms"], alpha=M["alpha"], T=M["T"], dt=cfg["dt"],
+                                 mode=cfg["mode"], Tc=M["Tc"], H_start_Oe=cfg["H_start"],
+                                 H_turn_Oe=cfg["H_turn"], rate_Oe_per_ns=cfg["rate"])
+
+
+def _oracle_steps_for(O, p, cfg, n_real, threads, budget_s):
+    """Heun steps of n_real rods that take about budget_s on the host cores (from a 20-step
+    calibration run)."""
     m = O.uniform_state(n_real, p.ncells)
     t0 = time.perf_counter()
     O.run(p, m, seed=cfg["seed"], n_steps=20, threads=threads)
     per_step = (time.perf_counter() - t0) / 20
-    steps = max(20, int(budget_s / max(per_step, 1e-9)))
+    return max(20, int(budget_s / max(per_step, 1e-9)))
+
+
+def _oracle_timed(O, p, cfg, n_real, steps, threads):
+    """Seconds of one oracle run of n_real rods from +z over `steps` Heun steps."""
     m = O.uniform_state(n_real, p.ncells)
     t0 = time.perf_counter()
     O.run(p, m, seed=cfg["seed"], n_steps=steps, threads=threads)
-    el = time.perf_counter() - t0
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_rate(cfg, budget_s=12.0):
+    """The FP64 oracle on the host cores on a bounded sample of the workload: rods of the same
+    size, a short window of Heun steps.  Returns (cell-steps/s, threads, description)."""
+    threads = os.cpu_count() or 1
+    O, p = _oracle_problem(cfg)
+    n_real = threads
+    steps = _oracle_steps_for(O, p, cfg, n_real, threads, budget_s)
+    el = _oracle_timed(O, p, cfg, n_real, steps, threads)
     rate = n_real * p.ncells * steps / el
     return rate, threads, (f"{n_real} b={cfg['b']} rods ({p.ncells} cells) x {steps} Heun steps "
                            f"from +z, FP64, {el:.1f} s")
@@ -198,32 +214,43 @@ def cpu_oracle_rate(cfg, budget_s=12.0):
 # ------------------------------------------------------------------------------------------------
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle (the only other implementation of the method here)
-    timed on the host cores, per step a bounded sample of the same workload."""
+    timed on the host cores.  A step is a bounded sample of the workload -- one rod per host
+    thread over a fixed number of Heun steps, sized so the whole run takes a few minutes -- and
+    the line reports what was measured: its time per step and its cell-steps/s.  The time the
+    oracle would need for one full step of the GPU arm (256 rods x one sample interval) is
+    extrapolated from that rate and labelled as such."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     from workloads import CONFIGS
     cfg = CONFIGS[WORKLOAD]
-    per_step_budget = max(2.0, min(20.0, 100.0 / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        cpu_oracle_rate(cfg, budget_s=per_step_budget / 4)
-    rates = []
-    desc = ""
     threads = os.cpu_count() or 1
-    for _ in range(args.steps):
-        r, threads, desc = cpu_oracle_rate(cfg, budget_s=per_step_budget)
-        rates.append(r)
-    value = statistics.mean(rates)
+    per_step_budget = max(2.0, min(20.0, 100.0 / max(1, args.steps + args.warmup)))
+    O, p = _oracle_problem(cfg)
+    n_real = threads
+    heun = _oracle_steps_for(O, p, cfg, n_real, threads, per_step_budget)
+    for _ in range(args.warmup):
+        _oracle_timed(O, p, cfg, n_real, max(20, heun // 4), threads)
+    secs = [_oracle_timed(O, p, cfg, n_real, heun, threads) for _ in range(args.steps)]
+    total = sum(secs)
     ncell = math.prod(cfg["dims"])
+    value = n_real * ncell * heun * args.steps / total
     steps_per_sample = round(cfg["sample_dH"] / (cfg["rate"] * 1e9 * cfg["dt"]))
-    step_cells = cfg["n_real"] * ncell * steps_per_sample
+    gpu_step_cells = cfg["n_real"] * ncell * steps_per_sample
+    desc = (f"{n_real} b={cfg['b']} rods ({ncell} cells) x {heun} Heun steps from +z per step, FP64, "
+            f"{total / args.steps:.1f} s per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_cells / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "rods": cfg["n_real"],
-                                        "cells_per_rod": ncell, "heun_steps_per_step": steps_per_sample,
-                                        "l2": "not applicable (host)"},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rods": n_real, "cells_per_rod": ncell,
+                   "heun_steps_measured": heun,
+                   "sample": "rods and steps measured per step (a bounded sample of the workload)",
+                   "extrapolated": True,
+                   "extrapolated_ms_per_full_step": 1e3 * gpu_step_cells / value,
+                   "full_step": f"{cfg['n_real']} rods x {steps_per_sample} Heun steps",
+                   "l2": "not applicable (host)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -272,13 +299,28 @@ def run_ours(args):
                                       device="cuda" if world > 1 else "cpu")
     if world > 1:
         torch.distributed.barrier()
+    # one ensemble over all ranks: the sample columns written so far, summed over ranks (an
+    # all-reduce of per-sample sums and sums of squares; outside the timed region)
+    from paper_1912_00310_gb300 import ensemble
+    k_done = args.warmup + args.steps
+    cols = samples[:, 1:k_done + 1].float().cpu().numpy()
+    n_tot, s1, s2 = ensemble.sample_moments(cols)
+    mean_mz = s1 / n_tot
+    se_mz = ((s2 - s1 * s1 / n_tot) / max(1, n_tot - 1) / n_tot) ** 0.5
+    ens = {"realisations": n_tot, "samples": int(cols.shape[1]),
+           "mean_mz_last": float(mean_mz[-1]), "se_mz_last": float(se_mz[-1]),
+           "reduction": "per-sample sums over ranks (all-reduce), llg_loop_moments"}
 
     steps_per_loop = g.steps_per_loop
     loops_per_s = value / (ncell * steps_per_loop)
     launch_s = local_total / args.steps  # one persistent launch per step
     achieved = ALU_OPS_PER_CELL_STEP * cells_per_step / launch_s
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sm_count * ALU_LANES_PER_SM * MAX_SM_MHZ * 1e6
+    nominal = sm_count * ALU_LANES_PER_SM * MAX_SM_MHZ * 1e6
+    # measured denominator: the FP32 lanes' issue rate on this GPU (outside the timed region)
+    alu = pkg.measure_alu_peak(dev)
+    peak = alu["ffma_lane_ops_per_s"]
+    ALU_PEAK["value"] = peak
 
     extra = {}
     if not args.quick:
@@ -307,10 +349,15 @@ def run_ours(args):
                          "traffic_unit": "bytes per launch (ncu dram read + write)",
                          "kernel": "rod_pipelined_nx_kernel<3, 8, 24, 56>",
                          "ops_per_cell_step": ALU_OPS_PER_CELL_STEP,
-                         "peak_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x {MAX_SM_MHZ:.0f} MHz"},
+                         "peak_basis": "measured: FP32 FMA issue microbenchmark (llg_measure_alu_peak) "
+                                       f"at {alu['ffma_sm_mhz']:.0f} MHz",
+                         "int_mix_lane_ops_per_s": alu["int_lane_ops_per_s"] / 1e9,
+                         "nominal_peak": nominal / 1e9,
+                         "nominal_basis": f"{sm_count} SMs x {ALU_LANES_PER_SM} lanes x {MAX_SM_MHZ:.0f} MHz"},
             "clocks": clk,
             "gpu_launches": args.steps,
             "cpu_baseline": cpu,
+            "ensemble": ens,
         }
         line.update(extra)
         print(json.dumps(line))
@@ -552,7 +599,8 @@ def slab_stream(args, torch, pkg, flush):
     return {"cells": ncells, "value": rate, "unit": UNIT, "ms_per_heun_step": 1e3 * t_step,
             "hbm_algorithmic_gbs": alg, "hbm_float4_gbs": phys, "hbm_peak_gbs": peak,
             "hbm_peak_basis": basis, "hbm_frac_algorithmic": alg / peak,
-            "alu_frac": ALU_OPS_PER_CELL_STEP * rate / (152 * ALU_LANES_PER_SM * MAX_SM_MHZ * 1e6),
+            "alu_frac": ALU_OPS_PER_CELL_STEP * rate / (ALU_PEAK["value"] or (152 * ALU_LANES_PER_SM * MAX_SM_MHZ * 1e6)),
+            "alu_peak_basis": "measured" if ALU_PEAK["value"] else "nominal",
             "l2": "state (470 MB ping-pong) larger than L2"}
 
 

@@ -175,6 +175,13 @@ llg_status llg_set_engine(llg_ctx *ctx, int engine);
  *                             segment by segment.  The states, and so the loss, are the same
  *                             either way; the gradient's partial sums are grouped differently
  *                             (to about 1e-7 relative).
+ *   LLG_TUNE_HANDOFF_TIMEOUT_MS  longest wait (ms, default 30000, 1 .. 3600000) of a CTA of the
+ *                             balanced schedule for the CTA that runs the first part of a rod it
+ *                             finishes; on expiry the CTA skips its remaining segments, and the
+ *                             next llg_sync returns ETIMEOUT (the ensemble is then incomplete:
+ *                             reset or restore it)
+ *   LLG_TUNE_WITHHOLD_HANDOFF 1: failure-path test hook -- the balanced schedule's producers do
+ *                             not signal their hand-offs, so every wait runs out (default 0)
  * The arithmetic, and so the trajectory, does not depend on these.  Errors: EINVAL (unknown
  * key, negative value); EUNSUPPORTED at the next advance if the shape cannot hold the grid. */
 #define LLG_TUNE_ROD_KIND 1
@@ -184,6 +191,8 @@ llg_status llg_set_engine(llg_ctx *ctx, int engine);
 #define LLG_TUNE_GENERIC_KERNEL 5
 #define LLG_TUNE_BALANCE 6
 #define LLG_TUNE_ADJOINT_STATE_MB 7
+#define LLG_TUNE_HANDOFF_TIMEOUT_MS 8
+#define LLG_TUNE_WITHHOLD_HANDOFF 9
 llg_status llg_set_tuning(llg_ctx *ctx, int key, int64_t value);
 
 /* ---------------------------------------------------------------------------------------- */
@@ -298,6 +307,47 @@ llg_status llg_loop_stats_host(const float *m_samples, int n_real, int64_t n_sam
                                const double *H_Oe, int64_t k_turn, int mode, double zeta,
                                double delta, llg_loop_stats *out, double *mean_out);
 
+/* The same observables for an ensemble whose realisations are split over several processes
+ * (one per GPU; the realisations of the loop paragraph are independent).  The exchange is two
+ * small sums across processes:
+ *   1. llg_loop_moments on each process: per-sample sums sum_out [n_samples] (and, optional,
+ *      sums of squares sumsq_out) of its own realisations, in FP64; the processes add them and
+ *      their realisation counts (n_total);
+ *   2. llg_loop_jackknife_terms on each process: given the global sums sum_all, the delete-one
+ *      jackknife terms of its own n_local realisations, out = {sum d_Hc, sum d_Hc^2, sum d_area,
+ *      sum d_area^2} with d = (statistic of the mean loop without that realisation) - (statistic
+ *      of the full mean loop); the processes add the four numbers;
+ *   3. llg_loop_stats_from_sums: the observables of the global mean loop and their jackknife
+ *      standard errors from the global sums and terms (jk NULL: no standard errors).
+ * Over one process this is llg_loop_stats_host (which is implemented this way).  All host memory;
+ * no GPU needed.  Errors: EINVAL. */
+llg_status llg_loop_moments(const float *m_samples, int n_real, int64_t n_samples, double *sum_out,
+                            double *sumsq_out);
+llg_status llg_loop_jackknife_terms(const float *m_samples, int n_local, int64_t n_samples,
+                                    const double *sum_all, int n_total, const double *H_Oe,
+                                    int64_t k_turn, double out[4]);
+llg_status llg_loop_stats_from_sums(const double *sum_all, int n_total, int64_t n_samples,
+                                    const double *H_Oe, int64_t k_turn, const double jk[4], int mode,
+                                    double zeta, double delta, llg_loop_stats *out, double *mean_out);
+
+/* Specific loss power (the SR/alpha paragraph's heating figure): a loop of area area_Oe (the
+ * closed integral of m dH, Oe) dissipates mu0 Ms area per cycle and unit volume (H in A/m), so at
+ * frequency f_hz the power per mass is f mu0 Ms (1000/4pi) area / rho, here in W/g with the
+ * density rho_kg_m3 in kg/m^3.  Errors: EINVAL (f < 0, Ms <= 0, rho <= 0, non-finite area). */
+llg_status llg_specific_loss_power(double f_hz, double Ms, double area_Oe, double rho_kg_m3,
+                                   double *W_per_g);
+
+/* Measured issue rates of the SM's 32-bit lanes on `device` (the ALU roofline denominator of the
+ * resident and streaming kernels, which are bound by 32-bit lane operations): out[0] FP32
+ * fused multiply-adds per second (eight independent chains per thread, 64 warps per SM), out[1]
+ * the median SM clock (MHz) during that kernel, from the SM cycle counter against the global
+ * timer, out[2] lane operations per second of the noise generator's integer mix (Philox rounds,
+ * counted as in the algorithmic lane-op count: a 32x32->64 product = 2, a 3-input xor = 2),
+ * out[3] the SM clock during that kernel.  Best of five timed launches of about 10-50 ms each;
+ * synchronises; allocates a few KB.  No clock or other device setting is changed.
+ * Errors: EINVAL (device), ECUDA. */
+llg_status llg_measure_alu_peak(int device, double out[4]);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Allocation-free advance (no counterpart in the paper)                                     */
 /* ---------------------------------------------------------------------------------------- */
@@ -319,13 +369,16 @@ llg_status llg_loop_stats_host(const float *m_samples, int n_real, int64_t n_sam
  *   m_samples  device [n_real][llg_num_samples] or NULL, written as llg_advance does
  *   cuda_stream  stream for the work; the call is asynchronous unless status_out is given
  *   status_out host or NULL: when given, the call waits for the stream and stores 1 if a
- *              non-finite sample was seen, else 0
+ *              non-finite sample was seen, else 0.  It must be NULL while the stream is being
+ *              captured (the read-back and the wait are not capturable): EINVAL otherwise.
+ * The work runs on the current device, which must be the context's device; m and m_samples must
+ * be memory of that device (EINVAL otherwise, checked before anything is enqueued).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture begins.  All calls share
  * the one array and the status word is cleared at the start of each call, so calls whose GPU work
  * overlaps (other streams, other host threads) race and must be serialised by the caller.
  * Errors: EINVAL (n_real * ncells above LLG_NOALLOC_MAX_CELL_REALISATIONS, bad arguments, setup
- * incomplete), ECUDA. */
+ * incomplete, wrong current device, buffers not on it, status_out during capture), ECUDA. */
 llg_status llg_plain_advance_noalloc(const llg_ctx *ctx, float *m, int n_real, uint32_t seed,
                                      uint32_t real_offset, int64_t step0, int64_t n_steps,
                                      float *m_samples, void *cuda_stream, int *status_out);

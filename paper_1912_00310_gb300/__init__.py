@@ -11,14 +11,15 @@ import numpy as np
 
 from . import _lib
 from ._lib import (COEFF_NAMES, ENGINE_AUTO, ENGINE_PLAIN, ENGINE_RESIDENT, ENGINE_STREAM,
-                   TUNE_ADJOINT_STATE_MB, TUNE_BALANCE, TUNE_CHUNK_STEPS, TUNE_GENERIC_KERNEL, TUNE_ROD_KIND, TUNE_RODS_PER_CTA,
-                   TUNE_ROWS_PER_THREAD, LLGError,
-                   LoopStats)
+                   TUNE_ADJOINT_STATE_MB, TUNE_BALANCE, TUNE_CHUNK_STEPS, TUNE_GENERIC_KERNEL,
+                   TUNE_HANDOFF_TIMEOUT_MS, TUNE_ROD_KIND, TUNE_RODS_PER_CTA, TUNE_ROWS_PER_THREAD,
+                   TUNE_WITHHOLD_HANDOFF, LLGError, LoopStats)
 
-__all__ = ["Grid", "run_batch", "loop_loss", "LLGError", "LoopStats", "loop_stats", "gk_flow", "ENGINE_AUTO", "ENGINE_RESIDENT",
+__all__ = ["Grid", "run_batch", "loop_loss", "LLGError", "LoopStats", "loop_stats", "gk_flow",
+           "specific_loss_power", "measure_alu_peak", "ENGINE_AUTO", "ENGINE_RESIDENT",
            "ENGINE_PLAIN", "ENGINE_STREAM", "TUNE_ROD_KIND", "TUNE_RODS_PER_CTA", "TUNE_CHUNK_STEPS",
            "TUNE_ROWS_PER_THREAD", "TUNE_GENERIC_KERNEL", "TUNE_BALANCE", "TUNE_ADJOINT_STATE_MB",
-           "library"]
+           "TUNE_HANDOFF_TIMEOUT_MS", "TUNE_WITHHOLD_HANDOFF", "library"]
 
 
 def library():
@@ -249,6 +250,22 @@ def gk_flow(Tstar0: float, h0: float, g0: float, b: float, n_steps: int = 4000) 
     out = (C.c_double * 4)()
     _lib.check(_lib.load().llg_gk_flow(Tstar0, h0, g0, b, int(n_steps), out))
     return dict(zip(["Tstar", "h", "g", "zeta"], list(out)))
+
+
+def specific_loss_power(f_hz: float, Ms: float, area_Oe: float, rho_kg_m3: float) -> float:
+    """Specific loss power (W/g) of a loop of area area_Oe at frequency f_hz:
+    f mu0 Ms (1000/4 pi) area / rho (the SR/alpha paragraph's heating figure)."""
+    out = C.c_double()
+    _lib.check(_lib.load().llg_specific_loss_power(f_hz, Ms, area_Oe, rho_kg_m3, C.byref(out)))
+    return out.value
+
+
+def measure_alu_peak(device: int = 0) -> dict:
+    """Measured 32-bit lane issue rates of the GPU (llg_measure_alu_peak)."""
+    out = (C.c_double * 4)()
+    _lib.check(_lib.load().llg_measure_alu_peak(device, out))
+    return dict(ffma_lane_ops_per_s=out[0], ffma_sm_mhz=out[1], int_lane_ops_per_s=out[2],
+                int_sm_mhz=out[3])
 
 
 def loop_stats(samples: np.ndarray, H: np.ndarray, k_turn: int, mode=1, zeta=1.0, delta=0.511):

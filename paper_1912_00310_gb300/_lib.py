@@ -21,6 +21,7 @@ STATUS = {0: "LLG_OK", 1: "LLG_EINVAL", 2: "LLG_ENOMEM", 3: "LLG_ECUDA", 4: "LLG
 ENGINE_AUTO, ENGINE_RESIDENT, ENGINE_PLAIN, ENGINE_STREAM = 0, 1, 2, 3
 TUNE_ROD_KIND, TUNE_RODS_PER_CTA, TUNE_CHUNK_STEPS, TUNE_ROWS_PER_THREAD = 1, 2, 3, 4
 TUNE_GENERIC_KERNEL, TUNE_BALANCE, TUNE_ADJOINT_STATE_MB = 5, 6, 7
+TUNE_HANDOFF_TIMEOUT_MS, TUNE_WITHHOLD_HANDOFF = 8, 9
 
 
 class LoopStats(C.Structure):
@@ -79,6 +80,12 @@ SIGNATURES = {
                                             _fp, _vp, C.POINTER(C.c_int)]),
     "llg_loop_stats_host": (C.c_int, [_fp, C.c_int, _i64, _dp, _i64, C.c_int, C.c_double,
                                       C.c_double, C.POINTER(LoopStats), _dp]),
+    "llg_loop_moments": (C.c_int, [_fp, C.c_int, _i64, _dp, _dp]),
+    "llg_loop_jackknife_terms": (C.c_int, [_fp, C.c_int, _i64, _dp, C.c_int, _dp, _i64, _dp]),
+    "llg_loop_stats_from_sums": (C.c_int, [_dp, C.c_int, _i64, _dp, _i64, _dp, C.c_int, C.c_double,
+                                           C.c_double, C.POINTER(LoopStats), _dp]),
+    "llg_specific_loss_power": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, _dp]),
+    "llg_measure_alu_peak": (C.c_int, [C.c_int, _dp]),
 }
 
 _lib = None

@@ -35,6 +35,8 @@ struct llg_ctx {
     int tune_kind = 0, tune_rods = 0, tune_rows = 0, tune_generic = 0, tune_balance = 1;
     long long adjoint_state_mb = 16384;  // budget for the adjoint's stored window states
     long long chunk_steps = 1LL << 20;
+    long long handoff_timeout_ms = 30000;  // balanced resident schedule: longest hand-off wait
+    int withhold_handoff = 0;              // test hook: the hand-offs are never released
     // ensemble
     int n_real = 0;
     uint32_t seed = 0, real0 = 0;
@@ -172,6 +174,8 @@ int resolve_engine(const llg_ctx *c, const llg::KParams &kp, int n_real, llg::Ro
     const bool rod_ok = llg::rod_plan(kp, n_real, c->device, plan, c->tune_kind, c->tune_rods, c->tune_rows);
     plan->generic = c->tune_generic != 0;
     plan->balance = c->tune_balance != 0;
+    plan->handoff_timeout_ns = (unsigned long long)c->handoff_timeout_ms * 1000000ull;
+    plan->withhold_handoff = c->withhold_handoff != 0;
     llg::SlabPlan tmp;
     const bool slab_ok = llg::slab_plan(kp, c->device, splan ? splan : &tmp);
     switch (c->engine) {
@@ -239,6 +243,8 @@ llg_status kparams_from_ctx(const llg_ctx *c, KParams *out)
     *out = kparams_of(d, c->nx, c->ny, c->nz, c->periodic, c->sw.dt);
     return LLG_OK;
 }
+
+int ctx_device(const llg_ctx *c) { return c->device; }
 }  // namespace llg
 
 extern "C" {
@@ -448,6 +454,13 @@ llg_status llg_set_tuning(llg_ctx *c, int key, int64_t value)
         case LLG_TUNE_ADJOINT_STATE_MB:
             if (value > (1LL << 22)) return fail(LLG_EINVAL, "at most 4 TB for the adjoint's states");
             c->adjoint_state_mb = value;
+            return LLG_OK;
+        case LLG_TUNE_HANDOFF_TIMEOUT_MS:
+            if (value < 1 || value > 3600000) return fail(LLG_EINVAL, "hand-off timeout must be 1 ms .. 1 h");
+            c->handoff_timeout_ms = value;
+            return LLG_OK;
+        case LLG_TUNE_WITHHOLD_HANDOFF:
+            c->withhold_handoff = value != 0;
             return LLG_OK;
         case LLG_TUNE_CHUNK_STEPS:
             if (value > (1LL << 30)) return fail(LLG_EINVAL, "at most 2^30 steps per launch");

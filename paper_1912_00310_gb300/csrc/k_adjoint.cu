@@ -26,8 +26,9 @@
 // With memory to spare (the whole window's states, 12 bytes per cell, realisation and step), one
 // launch recomputes every segment at once (a CTA per rod and segment) and one launch walks the
 // whole window back, so the recomputation leaves the sequential critical path; otherwise each
-// segment is recomputed and reversed in turn in one launch.  Parameter partial sums are FP64 per
-// thread and per CTA.
+// segment is recomputed and reversed in turn in one launch.  The parameter partial sums are FP32
+// within blocks of 64 steps (aligned to absolute step numbers) and FP64 across blocks and in the
+// per-CTA reduction.
 #include <cmath>
 
 #include "llg_internal.h"

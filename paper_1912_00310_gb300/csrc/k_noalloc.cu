@@ -54,6 +54,19 @@ cudaError_t scratch_address(int device, float **out)
     return cudaSuccess;
 }
 
+// True when p is device memory of `device` (or managed memory): host pointers and other
+// devices' memory are refused before anything is enqueued.
+bool on_device(const void *p, int device)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
+}
+
 }  // namespace
 
 extern "C" llg_status llg_plain_advance_noalloc(const llg_ctx *ctx, float *m, int n_real, uint32_t seed,
@@ -71,15 +84,33 @@ extern "C" llg_status llg_plain_advance_noalloc(const llg_ctx *ctx, float *m, in
         return error(LLG_EINVAL,
                      "%d realisations x %lld cells exceed the allocation-free scratch of %d cell-realisations",
                      n_real, ncells, LLG_NOALLOC_MAX_CELL_REALISATIONS);
+    // The work runs on the current device, which must be the context's; the state and the
+    // sample buffer must be that device's memory (another GPU's pointer would be dereferenced
+    // without peer access).
     int device = 0;
     cudaError_t e = cudaGetDevice(&device);
-    if (e == cudaSuccess && (device < 0 || device >= kMaxDevices)) e = cudaErrorInvalidDevice;
+    if (e != cudaSuccess) return error(LLG_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (device != llg::ctx_device(ctx))
+        return error(LLG_EINVAL, "the current device (%d) is not the context's device (%d)", device,
+                     llg::ctx_device(ctx));
+    if (!on_device(m, device) || (m_samples && !on_device(m_samples, device)))
+        return error(LLG_EINVAL, "m and m_samples must be device memory of device %d", device);
+    const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // status_out needs a device-to-host read and a stream synchronisation, which a stream that is
+    // being captured cannot take
+    if (status_out) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            return error(LLG_EINVAL, "status_out must be NULL while the stream is being captured");
+        }
+    }
+    if (device < 0 || device >= kMaxDevices) return error(LLG_EINVAL, "device ordinal %d too large", device);
     float *base = nullptr;
-    if (e == cudaSuccess) e = scratch_address(device, &base);
+    e = scratch_address(device, &base);
     if (e != cudaSuccess) return error(LLG_ECUDA, "scratch set-up: %s", cudaGetErrorString(e));
     kp.seed = seed;
     kp.real0 = real_offset;
-    const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     int *status = reinterpret_cast<int *>(base);
     float *work = base + kHeaderFloats;
     const size_t per = (size_t)n_real * (size_t)ncells * 3;

@@ -618,29 +618,25 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
-// Longest a CTA waits for the first part of a rod it finishes before giving up (the producer
-// normally finished long before: it ran the first part at the start of its own schedule).
-constexpr unsigned long long kHandoffTimeoutNs = 30ull * 1000 * 1000 * 1000;
-
-// Balanced schedule of one launch: up to three segments per CTA {rod, first step offset, steps,
-// kind}, kind 0 = whole rod or plain part, 1 = first part (signal flags[rod] when done),
-// 2 = last part (wait for flags[rod] first).  Built on the host (McNaughton's wrap-around rule:
-// all n_real * n_steps rod-steps laid end to end and cut into gridDim.x equal slices; a rod cut at
-// a slice boundary runs its first steps at the start of the next CTA's slice and its last steps
-// at the end of this CTA's slice).  Passed as a kernel parameter so the segment fields are
-// uniform (constant-bank) values.
-constexpr int kMaxBalancedCtas = 256;
-struct BalancedSchedule {
-    int4 seg[3 * kMaxBalancedCtas];
+// Hand-off of the balanced schedule (McNaughton's wrap-around rule): all n_real * N rod-steps of
+// a launch laid end to end (rod r at positions [r N, (r + 1) N)) and cut into gridDim.x equal
+// slices of C = ceil(n_real N / gridDim.x) >= N positions.  A CTA walks its slice in order: a rod
+// cut at the slice's start is run for its FIRST steps (kind 1, then flags[rod] is released), whole
+// rods are run entirely (kind 0), and a rod cut at the slice's end is run for its LAST steps
+// (kind 2, after waiting for flags[rod]).  Because C >= N, the producer of a hand-off runs it at
+// the start of its own slice, long before the consumer reaches the end of its slice.  The schedule
+// is arithmetic on (n_real, N, gridDim.x), so each CTA derives its own segments.
+struct HandoffCtl {
+    unsigned long long timeout_ns;  // longest wait for a producer before giving up (status bit 1)
+    int withhold;                   // test hook: producers do not release (every wait runs out)
 };
 
 // balanced == 0: one rod per CTA over [step0, step0 + n_steps).
-// balanced == 1: the segments of `sched`; needs all CTAs co-resident (cooperative launch).
+// balanced == 1: the wrap-around schedule above; needs all CTAs co-resident (cooperative launch).
 template <int R, int NX, int NY = 0, int NZ = 0, int SHAPE = -1, bool AX = false>
 __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_kernel(
-    KParams p, float *__restrict__ m_glob, long long step0, int n_steps, float *__restrict__ samples,
-    int *__restrict__ status, unsigned *__restrict__ flags, int balanced,
-    const __grid_constant__ BalancedSchedule sched)
+    KParams p, float *__restrict__ m_glob, long long step0, int n_steps, int n_real, float *__restrict__ samples,
+    int *__restrict__ status, unsigned *__restrict__ flags, int balanced, HandoffCtl hc)
 {
     static_assert(NX >= 3 && NX % 2 == 0, "merged schedule with even plane count");
     extern __shared__ float4 sm4[];
@@ -650,16 +646,27 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_
     w.setup(sm4, p);
     __syncthreads();
     __shared__ int go;
-    const int nseg = balanced ? 3 : 1;
-    for (int i = 0; i < nseg; ++i) {
-        const int4 sg = balanced ? sched.seg[3 * blockIdx.x + i] : make_int4(blockIdx.x, 0, n_steps, 0);
-        if (sg.z <= 0) continue;
-        if (sg.w == 2) {
+    if (!balanced) {
+        w.run(p, m_glob, blockIdx.x, step0, n_steps, samples, status);
+        return;
+    }
+    const long long N = n_steps;
+    const long long W = (long long)n_real * N;
+    const long long C = (W + gridDim.x - 1) / gridDim.x;
+    const long long lo = min((long long)blockIdx.x * C, W), hi = min(lo + C, W);
+    for (long long pos = lo; pos < hi;) {
+        const int rod = (int)(pos / N);
+        const long long off = pos - (long long)rod * N;
+        const long long len = min(hi, (long long)(rod + 1) * N) - pos;
+        // kind 1: the rod's first len steps; kind 2: its last len steps; kind 0: all of it
+        const int kind = off != 0 ? 1 : (len < N ? 2 : 0);
+        pos += len;
+        if (kind == 2) {
             if (threadIdx.x == 0) {
                 const unsigned long long t0 = globaltimer_ns();
                 int ok = 1;
-                while (ld_acquire_gpu(flags + sg.x) == 0u) {
-                    if (globaltimer_ns() - t0 > kHandoffTimeoutNs) {
+                while (ld_acquire_gpu(flags + rod) == 0u) {
+                    if (globaltimer_ns() - t0 > hc.timeout_ns) {
                         ok = 0;
                         atomicOr(status, 2);
                         break;
@@ -672,10 +679,10 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_
             __syncthreads();
             if (!go) break;
         }
-        w.run(p, m_glob, sg.x, step0 + sg.y, sg.z, samples, status);
-        if (sg.w == 1 && threadIdx.x == 0) {
+        w.run(p, m_glob, rod, step0 + (kind == 2 ? N - len : 0), len, samples, status);
+        if (kind == 1 && threadIdx.x == 0 && !hc.withhold) {
             __threadfence();
-            st_release_gpu(flags + sg.x, 1u);
+            st_release_gpu(flags + rod, 1u);
         }
     }
 }
@@ -781,38 +788,6 @@ static cudaError_t set_smem(K kernel, size_t bytes)
 
 // Launch of the nx-specialised kernel: balanced over a co-resident grid when the rods do not
 // divide evenly into waves, else one rod per CTA.
-// McNaughton's wrap-around schedule of n_real rods x N steps over G co-resident CTAs.
-static void balanced_schedule(int n_real, int N, int G, BalancedSchedule *sc)
-{
-    std::memset(sc, 0, sizeof *sc);
-    const long long W = (long long)n_real * N;
-    const long long C = (W + G - 1) / G;
-    for (int j = 0; j < G; ++j) {
-        const long long lo = std::min((long long)j * C, W), hi = std::min(lo + C, W);
-        int k = 0;
-        for (long long pos = lo; pos < hi && k < 3;) {
-            const long long rod = pos / N, off = pos - rod * N;
-            const long long len = std::min(hi, (rod + 1) * N) - pos;
-            int4 &g = sc->seg[3 * j + k++];
-            g.x = (int)rod;
-            g.z = (int)len;
-            if (off != 0) {  // first len steps, then hand off
-                g.y = 0;
-                g.w = 1;
-            } else if (len < N) {  // last len steps, after the hand-off
-                g.y = (int)(N - len);
-                g.w = 2;
-            } else {
-                g.y = 0;
-                g.w = 0;
-            }
-            pos += len;
-        }
-    }
-}
-
-// Launch of the nx-specialised kernel: balanced over a co-resident grid when the rods do not
-// divide evenly into waves, else one rod per CTA.
 template <int R, int NX, int NY = 0, int NZ = 0, bool AX = false>
 static cudaError_t launch_nx(const KParams &p, const RodPlan &plan, float *m, int n_real, long long step0,
                              long long n_steps, float *samples, int *status, unsigned *flags,
@@ -827,19 +802,17 @@ static cudaError_t launch_nx(const KParams &p, const RodPlan &plan, float *m, in
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, plan.threads, plan.smem_bytes)) != cudaSuccess)
         return e;
     const int resident = nsm * per_sm;
-    BalancedSchedule sched;  // kernel parameter (copied at launch)
-    int ns = (int)n_steps;
-    if (plan.balance && flags && resident > 0 && resident <= kMaxBalancedCtas && n_real > resident &&
-        n_real % resident != 0) {
-        balanced_schedule(n_real, ns, resident, &sched);
+    int ns = (int)n_steps;  // rod_advance splits longer runs
+    HandoffCtl hc{plan.handoff_timeout_ns, plan.withhold_handoff ? 1 : 0};
+    if (plan.balance && flags && resident > 0 && n_real > resident && n_real % resident != 0) {
         if ((e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)n_real, st)) != cudaSuccess) return e;
         int balanced = 1;
-        void *args[] = {(void *)&p, (void *)&m, (void *)&step0, (void *)&ns, (void *)&samples,
-                        (void *)&status, (void *)&flags, (void *)&balanced, (void *)&sched};
+        void *args[] = {(void *)&p, (void *)&m, (void *)&step0, (void *)&ns, (void *)&n_real, (void *)&samples,
+                        (void *)&status, (void *)&flags, (void *)&balanced, (void *)&hc};
         return cudaLaunchCooperativeKernel((const void *)kern, dim3(resident), dim3(plan.threads), args,
                                            plan.smem_bytes, st);
     }
-    kern<<<n_real, plan.threads, plan.smem_bytes, st>>>(p, m, step0, ns, samples, status, flags, 0, sched);
+    kern<<<n_real, plan.threads, plan.smem_bytes, st>>>(p, m, step0, ns, n_real, samples, status, flags, 0, hc);
     return cudaGetLastError();
 }
 
@@ -848,6 +821,18 @@ cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_r
                         unsigned *flags, cudaStream_t st)
 {
     if (n_steps <= 0) return cudaSuccess;
+    // the kernels count the steps of one launch in 32 bits: longer runs are split (the noise and
+    // the field are functions of the absolute step index, so the split changes nothing)
+    constexpr long long kMaxStepsPerLaunch = 1LL << 30;
+    if (n_steps > kMaxStepsPerLaunch) {
+        for (long long done = 0; done < n_steps; done += kMaxStepsPerLaunch) {
+            const cudaError_t e = rod_advance(p, plan, m, n_real, step0 + done,
+                                              std::min(kMaxStepsPerLaunch, n_steps - done), samples, status,
+                                              flags, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     cudaError_t e = cudaSuccess;
     if (plan.kind == 1) {
 #define LLG_TWOPHASE(C)                                                                         \

@@ -112,6 +112,8 @@ struct RodPlan {
     int ctas;
     bool generic = false;  // kind 2: use the runtime-nx kernel even where a specialised one exists
     bool balance = true;   // kind 2: balance rod-steps over a co-resident grid (needs flags)
+    unsigned long long handoff_timeout_ns = 30000000000ull;  // kind 2 balanced: longest hand-off wait
+    bool withhold_handoff = false;  // test hook: balanced producers never release (waits run out)
 };
 // Choose a launch plan for n_real rods of this grid on device `dev`; returns false if no
 // resident kernel can hold the rod.
@@ -162,6 +164,8 @@ namespace llg {
 // Kernel parameters of a context's grid, material, scaling and sweep (host-side derivation
 // only; seed and real0 are left zero).  Returns LLG_OK or the setup error (message stored).
 llg_status kparams_from_ctx(const llg_ctx *ctx, KParams *out);
+// The CUDA device ordinal a context was created for.
+int ctx_device(const llg_ctx *ctx);
 
 // A context's ensemble and launch settings, for the batching layer and the autotuner.  Makes
 // sure the hand-off flags of the resident engine exist when there is an ensemble.

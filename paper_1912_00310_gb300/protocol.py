@@ -24,7 +24,7 @@ import time
 
 import numpy as np
 
-from . import ENGINE_AUTO, Grid
+from . import ENGINE_AUTO, Grid, specific_loss_power
 
 MAGNETITE = dict(a0=0.839e-9, A0=0.98e-11, Ms=480e3, K0=10e3, alpha=0.1, T=310.0, Tc=858.0,
                  delta=0.511, rho=5170.0)  # rho: density (kg/m^3) of the specific loss power
@@ -63,10 +63,9 @@ def make_grid(b: int, *, H_max=500.0, rate=2.5, dt=None, alpha=None, disp_deg=5.
 
 
 def specific_loss_power_W_per_g(area_Oe: float, f_Hz: float) -> float:
-    """Specific loss power f mu0 (1000 / 4 pi) Ms S / rho of a loop of area S (Oe) at frequency f
-    (the SR/alpha paragraph), in W/g."""
-    mu0 = 4e-7 * math.pi
-    return f_Hz * mu0 * (1000.0 / (4.0 * math.pi)) * MAGNETITE["Ms"] * area_Oe / MAGNETITE["rho"] / 1000.0
+    """Specific loss power of magnetite (W/g) for a loop of area S (Oe) at frequency f (the
+    SR/alpha paragraph), computed by the library (llg_specific_loss_power)."""
+    return specific_loss_power(f_Hz, MAGNETITE["Ms"], area_Oe, MAGNETITE["rho"])
 
 
 def run(b: int, n_real: int, seed: int = 0, *, tune=True, paper=PAPER_AREA_OE, **kw) -> dict:

@@ -138,3 +138,57 @@ def test_gk_flow_matches_oracle(pkg, orc):
             assert mine[k] == pytest.approx(ref[k], rel=1e-12, abs=1e-300), (args, k)
     with pytest.raises(pkg.LLGError):
         pkg.gk_flow(1.0, 0.0, 0.0, 0.5)
+
+
+def test_specific_loss_power_matches_oracle(pkg, orc):
+    # the library's formula against the oracle's (whose energy per cycle is pinned by the energy
+    # balance of Eq. 1 in test_oracle_loops.py); rho in kg/m^3 against g/cm^3
+    for f, Ms, S in ((125e3, 480e3, 171.3), (1e5, 3e5, 12.5), (0.0, 480e3, 400.0)):
+        assert pkg.specific_loss_power(f, Ms, S, 5170.0) == pytest.approx(
+            orc.specific_loss_power(f, Ms, S, 5.17), rel=1e-12, abs=1e-300)
+    assert pkg.specific_loss_power(125e3, 480e3, 171.3, 5170.0) == pytest.approx(198.8, abs=0.05)
+    with pytest.raises(pkg.LLGError):
+        pkg.specific_loss_power(1e5, 0.0, 100.0, 5170.0)
+
+
+def test_loop_stats_from_sums_equal_host_statistics(pkg):
+    """The three-call distributed form over one process reproduces llg_loop_stats_host, and a
+    split of the realisations into two parts, combined by adding the parts' sums, gives the same
+    observables (what two processes exchange)."""
+    from paper_1912_00310_gb300 import ensemble
+    rng = np.random.default_rng(5)
+    n_half, R = 200, 24
+    H = np.concatenate([np.linspace(250, -250, n_half + 1), np.linspace(-250, 250, n_half + 1)[1:]])
+    k = np.arange(len(H))
+    S = np.stack([np.where(k <= n_half, np.tanh((H + h) / 25.0), np.tanh((H - h) / 25.0))
+                  for h in rng.normal(70.0, 9.0, size=R)]).astype(np.float32)
+    S += rng.normal(0, 0.02, size=S.shape).astype(np.float32)
+    ref = pkg.loop_stats(S, H, n_half, mode=2, zeta=0.72902, delta=0.511)
+    one = ensemble.loop_stats(S, H, n_half, mode=2, zeta=0.72902, delta=0.511)
+    for key in ("Hc_Oe", "Hc_se_Oe", "area_Oe", "area_se_Oe", "area0_Oe", "Hc0_Oe"):
+        assert one[key] == pytest.approx(ref[key], rel=1e-12), key
+    assert one["n_real"] == R
+    # two parts, sums added by hand
+    import ctypes as C
+    L = pkg.library()
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    parts = (S[:10], S[10:])
+    sums = []
+    for part in parts:
+        s1 = np.zeros(len(H))
+        assert L.llg_loop_moments(part.ctypes.data, part.shape[0], len(H), dp(s1), None) == 0
+        sums.append(s1)
+    total = sums[0] + sums[1]
+    jk = np.zeros(4)
+    for part in parts:
+        t = np.zeros(4)
+        part = np.ascontiguousarray(part)
+        assert L.llg_loop_jackknife_terms(part.ctypes.data, part.shape[0], len(H), dp(total), R, dp(H),
+                                          n_half, dp(t)) == 0
+        jk += t
+    st = pkg.LoopStats()
+    assert L.llg_loop_stats_from_sums(dp(total), R, len(H), dp(H), n_half, dp(jk), 2, 0.72902, 0.511,
+                                      C.byref(st), None) == 0
+    d = st.as_dict()
+    for key in ("Hc_Oe", "Hc_se_Oe", "area_Oe", "area_se_Oe"):
+        assert d[key] == pytest.approx(ref[key], rel=1e-10), key

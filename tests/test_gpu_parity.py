@@ -153,7 +153,7 @@ def test_b1_kernel_variants_bitwise_equal(pkg, dims):
         assert torch.equal(sm[:, 1:4], outs[0][1][:, 1:4])
 
 
-@pytest.mark.parametrize("n_real,steps", [(160, 2 * 50 + 7), (2 * 152 + 5, 50), (155, 3)])
+@pytest.mark.parametrize("n_real,steps", [(160, 2 * 50 + 7), (2 * 152 + 5, 50), (155, 3), (3 * 152 + 1, 7)])
 def test_balanced_schedule_is_bitwise_equal(pkg, n_real, steps):
     """More b = 1 rods than one wave: the balanced schedule (rods split between CTAs at step
     boundaries, hand-off through global memory) gives the same states and samples as one rod
@@ -320,6 +320,33 @@ def test_sync_timeout_then_recovery(pkg):
     assert e.value.status == 5
     g.sync(600)
     g.close()
+
+
+def test_handoff_wait_runs_out_then_recovery(pkg):
+    """The one device-side wait (a CTA of the balanced schedule waiting for the CTA that runs the
+    first part of a rod it finishes) is bounded: with the hand-offs withheld on purpose and a 1 ms
+    limit, every waiting CTA gives up, the launch ends, and llg_sync reports ETIMEOUT.  The same
+    context then runs normally, bitwise equal to one rod per CTA."""
+    dims, b, dt, n_real, steps = ROD_DIMS[1], 1, 2e-15, 160, 20
+    g = make_grid(pkg, dims, b, dt, engine=pkg.ENGINE_RESIDENT, rate=1e5, sample_dH=1.0)
+    g.set_tuning(pkg.TUNE_HANDOFF_TIMEOUT_MS, 1)
+    g.set_tuning(pkg.TUNE_WITHHOLD_HANDOFF, 1)
+    g.reset(seed=3, n_real=n_real)
+    g.advance(steps)
+    with pytest.raises(pkg.LLGError) as e:
+        g.sync(120)
+    assert e.value.status == 5 and "hand-off" in str(e.value)
+    g.set_tuning(pkg.TUNE_WITHHOLD_HANDOFF, 0)
+    g.reset(seed=3, n_real=n_real)
+    g.advance(steps)
+    g.sync(120)
+    ref = make_grid(pkg, dims, b, dt, engine=pkg.ENGINE_RESIDENT, rate=1e5, sample_dH=1.0)
+    ref.set_tuning(pkg.TUNE_BALANCE, 0)
+    ref.reset(seed=3, n_real=n_real)
+    ref.advance(steps)
+    assert torch.equal(state_of(g, n_real), state_of(ref, n_real))
+    g.close()
+    ref.close()
 
 
 def test_run_loops_host_and_device_buffers_agree(pkg):

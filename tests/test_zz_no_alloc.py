@@ -1,10 +1,13 @@
 """The allocation-free advance (llg_plain_advance_noalloc), called through the C ABI.
 
 It serves callers that cannot allocate device memory (inside stream capture, under a foreign
-allocator, in loops that cannot take an allocation's synchronisation).  Two calls in a row must
-reproduce the regular plain engine (llg_reset + llg_advance) on the same seeds within the
-trajectory tolerance of the other parity tests (1e-4), including the samples, and a request
-beyond the fixed scratch must be refused.  This file is collected last on purpose.
+allocator, in loops that cannot take an allocation's synchronisation).  It runs the same kernels
+with the same arithmetic as the regular plain engine (llg_reset + llg_advance), only with its
+scratch in a fixed library array, so two calls in a row must reproduce that engine on the same
+seeds bitwise, samples included (stricter than the 1e-4 trajectory tolerance of the other parity
+tests).  A request beyond the fixed scratch, and buffers that are not device memory of the
+context's device, must be refused before anything is launched.  This file is collected last on
+purpose.
 """
 import ctypes as C
 
@@ -56,12 +59,25 @@ def test_noalloc_matches_regular_plain_engine_over_two_calls():
         assert rc == 0, L.llg_last_error()
         assert status.value == 0
     torch.cuda.synchronize()
-    assert float((m - m_ref).abs().max()) <= 1e-4
+    assert torch.equal(m, m_ref)  # same kernels, same arithmetic: bitwise
     k = (first + second) // g.sample_every
     assert k == 4
     assert not torch.isnan(S[:, 1:k + 1]).any()
-    assert float((S[:, 1:k + 1] - S_ref[:, 1:k + 1]).abs().max()) <= 1e-4
+    assert torch.equal(S[:, 1:k + 1], S_ref[:, 1:k + 1])
     assert np.allclose(np.linalg.norm(m.cpu().numpy(), axis=-1), 1.0, atol=1e-6)
+
+    # a host buffer in place of device memory: refused, the device state untouched
+    m_before = m.clone()
+    host = np.zeros((n_real, g.ncells, 3), dtype=np.float32)
+    rc = L.llg_plain_advance_noalloc(g._h, C.c_void_p(host.ctypes.data), n_real, seed, off, 0, 1,
+                                     None, stream, None)
+    assert rc == 1
+    assert b"device memory" in L.llg_last_error()
+    rc = L.llg_plain_advance_noalloc(g._h, C.c_void_p(m.data_ptr()), n_real, seed, off, 0, 1,
+                                     C.c_void_p(host.ctypes.data), stream, None)
+    assert rc == 1
+    torch.cuda.synchronize()
+    assert torch.equal(m, m_before)
 
     # beyond the fixed scratch: refused with a clear message, nothing launched
     big = pkg.Grid(64, 64, 64, a0=M["a0"], b=1)
