@@ -420,6 +420,7 @@ def side_measurements(args, torch, pkg, cfg, g, samples, S_per_step, flush):
         g1.close()
     out["plain_same_workload"] = {"value": plain_rate, "unit": UNIT,
                                   "resident_over_plain": None}
+    out["rods_b4_608"] = small_rods_many(args, torch, pkg, flush)
     out["ladder_batch"] = ladder_batch(args, torch, pkg, flush)
     out["slab_512x512x56"] = slab_stream(args, torch, pkg, flush)
     out["adjoint_b4"] = adjoint_calibration(args, torch, pkg)
@@ -465,6 +466,27 @@ def hbm_peak_gbs():
     except (OSError, ValueError):
         pass
     return 6800.0, "fallback"
+
+
+def small_rods_many(args, torch, pkg, flush):
+    """The two-phase kernel on a full GPU of small rods: 608 b = 4 rods (2 x 6 x 14 cells, four per
+    SM), the plain-Heun workload's material and sweep, launch shape chosen by the autotuner."""
+    from workloads import CONFIGS
+    c1 = dict(CONFIGS["rod_b4_4real"])
+    n_real, W = 608, 20000
+    g = make_grid(pkg, c1, pkg.ENGINE_RESIDENT)
+    g.reset(seed=c1["seed"], n_real=n_real)
+    tuned = g.autotune(trial_steps=2000)
+    g.reset(seed=c1["seed"], n_real=n_real)
+    S = torch.zeros((n_real, g.n_samples), device="cuda")
+    ts = timed_steps(torch, lambda: g.advance(W, S), args.steps, 1, flush)
+    rate = n_real * g.ncells * W * args.steps / sum(ts)
+    shape = {k: g.tuning(k) for k in ("kind", "rods_per_cta", "cells_per_thread")}
+    g.close()
+    return {"rods": n_real, "cells_per_rod": math.prod(c1["dims"]), "heun_steps_per_call": W, "value": rate,
+            "unit": UNIT, "autotuned_rate": tuned, "launch_shape": shape,
+            "alu_frac": ALU_OPS_PER_CELL_STEP * rate / (ALU_PEAK["value"] or
+                                                        (152 * ALU_LANES_PER_SM * MAX_SM_MHZ * 1e6))}
 
 
 def ladder_batch(args, torch, pkg, flush):
@@ -666,6 +688,7 @@ def profile_case(name):
         n_real, steps = 160, (200 if name == "b1" else 5)
         eng = pkg.ENGINE_RESIDENT if name == "b1" else pkg.ENGINE_PLAIN
     elif name == "b4":
+        # 608 b = 4 rods with the autotuned two-phase launch shape
         cfg = dict(CONFIGS["rod_b4_4real"])
         n_real, steps, eng = 608, 2000, pkg.ENGINE_RESIDENT
     elif name == "slab":
@@ -689,6 +712,9 @@ def profile_case(name):
         raise SystemExit(f"unknown profile case {name}")
     g = make_grid(pkg, cfg, eng)
     g.reset(seed=0, n_real=n_real)
+    if name == "b4":
+        g.autotune(trial_steps=500)
+        g.reset(seed=0, n_real=n_real)
     S = torch.zeros((n_real, g.n_samples), device="cuda")
     for _ in range(3):
         g.advance(steps, S)

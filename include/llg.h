@@ -122,6 +122,12 @@ llg_status llg_set_scaling(llg_ctx *ctx, int mode, double Tc_kelvin, double delt
 llg_status llg_set_sweep(llg_ctx *ctx, double H_start_Oe, double H_turn_Oe, double rate_Oe_per_ns,
                          double dt_s, double sample_dH_Oe, int shape);
 
+/* For a held field (rate 0 in llg_set_sweep): n_samples sample columns, sample k taken after step
+ * k * sample_every (sample_dH of llg_set_sweep counts steps), for time averages at equilibrium
+ * (the temperature dependence of the magnetisation behind Eq. 12 and Fig. 3).  A later
+ * llg_set_sweep resets it to 1.  Errors: EINVAL (n_samples < 1, no sweep, a swept field). */
+llg_status llg_set_held_samples(llg_ctx *ctx, int64_t n_samples);
+
 /* Cell volume (m^3) of the thermal field in place of (b a0)^3, for the paper's single-block
  * limit: the whole rod as one rectangular-prism macrospin of volume 10752 a0^3 at b = 22 (the
  * simulation-cell paragraph).  0 restores (b a0)^3.  Errors: EINVAL (negative). */
@@ -162,7 +168,8 @@ llg_status llg_set_engine(llg_ctx *ctx, int engine);
 /* Launch-shape overrides of the resident engine (0 = automatic, the default):
  *   LLG_TUNE_ROD_KIND      1 two-phase kernel, 2 plane-pipelined kernel
  *   LLG_TUNE_RODS_PER_CTA  rods per CTA of the two-phase kernel
- *   LLG_TUNE_CHUNK_STEPS   Heun steps per launch (default 2^20)
+ *   LLG_TUNE_CHUNK_STEPS   Heun steps per launch (default 2^20; llg_autotune sets it so the
+ *                          launch overhead stays near 1% of a launch)
  *   LLG_TUNE_ROWS_PER_THREAD  rows per thread of the plane-pipelined kernel (1..4)
  *   LLG_TUNE_GENERIC_KERNEL   1: the runtime-size plane-pipelined kernel even where a kernel
  *                             specialised for the plane count exists
@@ -175,6 +182,9 @@ llg_status llg_set_engine(llg_ctx *ctx, int engine);
  *                             segment by segment.  The states, and so the loss, are the same
  *                             either way; the gradient's partial sums are grouped differently
  *                             (to about 1e-7 relative).
+ *   LLG_TUNE_CELLS_PER_THREAD cells per thread of the two-phase kernel (0 automatic, 1, 2, 4;
+ *                             the b = 4 and b = 8 rods get 768 / cells-per-thread threads per CTA
+ *                             at most, other grids 768)
  *   LLG_TUNE_HANDOFF_TIMEOUT_MS  longest wait (ms, default 30000, 1 .. 3600000) of a CTA of the
  *                             balanced schedule for the CTA that runs the first part of a rod it
  *                             finishes; on expiry the CTA skips its remaining segments, and the
@@ -193,7 +203,12 @@ llg_status llg_set_engine(llg_ctx *ctx, int engine);
 #define LLG_TUNE_ADJOINT_STATE_MB 7
 #define LLG_TUNE_HANDOFF_TIMEOUT_MS 8
 #define LLG_TUNE_WITHHOLD_HANDOFF 9
+#define LLG_TUNE_CELLS_PER_THREAD 10
 llg_status llg_set_tuning(llg_ctx *ctx, int key, int64_t value);
+
+/* The current value of a tuning key (as set, by llg_set_tuning or llg_autotune; 0 = automatic).
+ * Errors: EINVAL (unknown key, NULL argument). */
+llg_status llg_get_tuning(const llg_ctx *ctx, int key, int64_t *value);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Ensemble runs                                                                             */
@@ -241,7 +256,10 @@ llg_status llg_sync(llg_ctx *ctx, double timeout_s);
  * damping values at once): advance every job -- a context with an ensemble from llg_reset --
  * by min(max_steps, the steps left in its loop) Heun steps with the resident engine, all jobs in
  * one launch: a CUDA graph with one kernel node per job on independent branches, ordered
- * longest first, launched on jobs[0]'s stream after the work queued on every job's stream.
+ * longest first, launched on jobs[0]'s stream after the work queued on every job's stream.  A
+ * request of more steps than the jobs' smallest LLG_TUNE_CHUNK_STEPS runs as several such graph
+ * launches; the instantiated graph of a job set is cached (a few per process) and refreshed in
+ * place with cudaGraphExecUpdate.
  * m_samples (optional) [n_jobs] device sample arrays, one per job, as for llg_advance.
  * steps_done (optional, host) [n_jobs] receives the steps each job advanced.  Asynchronous.
  * Errors: EINVAL (no ensemble, jobs on different devices), EUNSUPPORTED (a grid the resident
@@ -250,10 +268,12 @@ llg_status llg_run_batch(llg_ctx *const *jobs, int n_jobs, int64_t max_steps,
                          float *const *m_samples, int64_t *steps_done);
 
 /* Choose the resident engine's launch shape for this context by timing the candidates (rows per
- * thread of the plane-pipelined kernel; rods per CTA of the two-phase kernel) for trial_steps
- * Heun steps each on a scratch copy of the ensemble (allocated and freed here), and set them
- * with llg_set_tuning.  Results are cached per (device, grid, realisation count) for the life of
- * the process.  The ensemble itself is not advanced.  best_rate (optional) receives the fastest
+ * thread of the plane-pipelined kernel; rods per CTA and cells per thread of the two-phase
+ * kernel) for trial_steps Heun steps each on a scratch copy of the ensemble (allocated and freed
+ * here), and set them with llg_set_tuning; also set the steps per launch (LLG_TUNE_CHUNK_STEPS)
+ * from the measured time of a one-step launch, so that the launch overhead stays near 1% of a
+ * launch.  Results are cached per (device, grid, realisation count) for the life of the
+ * process.  The ensemble itself is not advanced.  best_rate (optional) receives the fastest
  * cell-steps/s.  Synchronises.  Errors: EINVAL (no ensemble), ENOMEM, EUNSUPPORTED. */
 llg_status llg_autotune(llg_ctx *ctx, int64_t trial_steps, double *best_rate);
 

@@ -13,13 +13,13 @@ from . import _lib
 from ._lib import (COEFF_NAMES, ENGINE_AUTO, ENGINE_PLAIN, ENGINE_RESIDENT, ENGINE_STREAM,
                    TUNE_ADJOINT_STATE_MB, TUNE_BALANCE, TUNE_CHUNK_STEPS, TUNE_GENERIC_KERNEL,
                    TUNE_HANDOFF_TIMEOUT_MS, TUNE_ROD_KIND, TUNE_RODS_PER_CTA, TUNE_ROWS_PER_THREAD,
-                   TUNE_WITHHOLD_HANDOFF, LLGError, LoopStats)
+                   TUNE_WITHHOLD_HANDOFF, TUNE_CELLS_PER_THREAD, LLGError, LoopStats)
 
 __all__ = ["Grid", "run_batch", "loop_loss", "LLGError", "LoopStats", "loop_stats", "gk_flow",
            "specific_loss_power", "measure_alu_peak", "ENGINE_AUTO", "ENGINE_RESIDENT",
            "ENGINE_PLAIN", "ENGINE_STREAM", "TUNE_ROD_KIND", "TUNE_RODS_PER_CTA", "TUNE_CHUNK_STEPS",
            "TUNE_ROWS_PER_THREAD", "TUNE_GENERIC_KERNEL", "TUNE_BALANCE", "TUNE_ADJOINT_STATE_MB",
-           "TUNE_HANDOFF_TIMEOUT_MS", "TUNE_WITHHOLD_HANDOFF", "library"]
+           "TUNE_HANDOFF_TIMEOUT_MS", "TUNE_WITHHOLD_HANDOFF", "TUNE_CELLS_PER_THREAD", "library"]
 
 
 def library():
@@ -102,6 +102,11 @@ class Grid:
         _lib.check(self._L.llg_get_axes(self._h, C.c_void_p(_ptr(out))))
         return out
 
+    def set_held_samples(self, n_samples: int):
+        """Sample columns of a held (rate 0) field: sample k after step k * sample_every."""
+        _lib.check(self._L.llg_set_held_samples(self._h, int(n_samples)))
+        return self
+
     def set_cell_volume(self, volume_m3: float):
         _lib.check(self._L.llg_set_cell_volume(self._h, volume_m3))
         return self
@@ -113,6 +118,17 @@ class Grid:
     def set_tuning(self, key: int, value: int):
         _lib.check(self._L.llg_set_tuning(self._h, key, int(value)))
         return self
+
+    _TUNE_NAMES = {"kind": TUNE_ROD_KIND, "rods_per_cta": TUNE_RODS_PER_CTA, "chunk_steps": TUNE_CHUNK_STEPS,
+                   "rows_per_thread": TUNE_ROWS_PER_THREAD, "cells_per_thread": TUNE_CELLS_PER_THREAD}
+
+    def tuning(self, key) -> int:
+        """Current value of a tuning key (an LLG_TUNE_* number or one of kind, rods_per_cta,
+        chunk_steps, rows_per_thread, cells_per_thread)."""
+        k = self._TUNE_NAMES.get(key, key)
+        v = C.c_int64()
+        _lib.check(self._L.llg_get_tuning(self._h, int(k), C.byref(v)))
+        return v.value
 
     # ---- queries -----------------------------------------------------------------------
     @property

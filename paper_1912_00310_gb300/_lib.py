@@ -21,7 +21,7 @@ STATUS = {0: "LLG_OK", 1: "LLG_EINVAL", 2: "LLG_ENOMEM", 3: "LLG_ECUDA", 4: "LLG
 ENGINE_AUTO, ENGINE_RESIDENT, ENGINE_PLAIN, ENGINE_STREAM = 0, 1, 2, 3
 TUNE_ROD_KIND, TUNE_RODS_PER_CTA, TUNE_CHUNK_STEPS, TUNE_ROWS_PER_THREAD = 1, 2, 3, 4
 TUNE_GENERIC_KERNEL, TUNE_BALANCE, TUNE_ADJOINT_STATE_MB = 5, 6, 7
-TUNE_HANDOFF_TIMEOUT_MS, TUNE_WITHHOLD_HANDOFF = 8, 9
+TUNE_HANDOFF_TIMEOUT_MS, TUNE_WITHHOLD_HANDOFF, TUNE_CELLS_PER_THREAD = 8, 9, 10
 
 
 class LoopStats(C.Structure):
@@ -54,10 +54,12 @@ SIGNATURES = {
                                 C.c_int]),
     "llg_set_engine": (C.c_int, [_vp, C.c_int]),
     "llg_set_cell_volume": (C.c_int, [_vp, C.c_double]),
+    "llg_set_held_samples": (C.c_int, [_vp, _i64]),
     "llg_set_axis_dispersion": (C.c_int, [_vp, C.c_double]),
     "llg_gk_flow": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int64, _vp]),
     "llg_get_axes": (C.c_int, [_vp, _vp]),
     "llg_set_tuning": (C.c_int, [_vp, C.c_int, _i64]),
+    "llg_get_tuning": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int64)]),
     "llg_reset": (C.c_int, [_vp, C.c_uint32, C.c_int, C.c_uint32]),
     "llg_advance": (C.c_int, [_vp, _i64, _fp]),
     "llg_run_loops": (C.c_int, [_vp, C.c_uint32, C.c_int, C.c_uint32, _fp, C.POINTER(LoopStats)]),

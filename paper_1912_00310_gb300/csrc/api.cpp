@@ -32,7 +32,7 @@ struct llg_ctx {
     int ax_n = 0;
     double ax_disp = 0.0;
     int engine = LLG_ENGINE_AUTO;
-    int tune_kind = 0, tune_rods = 0, tune_rows = 0, tune_generic = 0, tune_balance = 1;
+    int tune_kind = 0, tune_rods = 0, tune_rows = 0, tune_generic = 0, tune_balance = 1, tune_cpt = 0;
     long long adjoint_state_mb = 16384;  // budget for the adjoint's stored window states
     long long chunk_steps = 1LL << 20;
     long long handoff_timeout_ms = 30000;  // balanced resident schedule: longest hand-off wait
@@ -171,7 +171,8 @@ struct DeviceGuard {
 int resolve_engine(const llg_ctx *c, const llg::KParams &kp, int n_real, llg::RodPlan *plan,
                    llg::SlabPlan *splan)
 {
-    const bool rod_ok = llg::rod_plan(kp, n_real, c->device, plan, c->tune_kind, c->tune_rods, c->tune_rows);
+    const bool rod_ok =
+        llg::rod_plan(kp, n_real, c->device, plan, c->tune_kind, c->tune_rods, c->tune_rows, c->tune_cpt);
     plan->generic = c->tune_generic != 0;
     plan->balance = c->tune_balance != 0;
     plan->handoff_timeout_ns = (unsigned long long)c->handoff_timeout_ms * 1000000ull;
@@ -229,6 +230,8 @@ llg_status ctx_view(llg_ctx *c, CtxView *v)
     v->tune_rods = c->tune_rods;
     v->tune_rows = c->tune_rows;
     v->tune_generic = c->tune_generic != 0;
+    v->tune_cpt = c->tune_cpt;
+    v->chunk_steps = c->chunk_steps;
     return LLG_OK;
 }
 
@@ -362,6 +365,22 @@ llg_status llg_set_sweep(llg_ctx *c, double H_start_Oe, double H_turn_Oe, double
     return LLG_OK;
 }
 
+llg_status llg_set_held_samples(llg_ctx *c, int64_t n_samples)
+{
+    if (!c) return fail(LLG_EINVAL, "ctx is NULL");
+    if (n_samples < 1) return fail(LLG_EINVAL, "n_samples must be >= 1");
+    if (!c->has_sweep) return fail(LLG_EINVAL, "sweep not set (llg_set_sweep)");
+    llg::Derived d;
+    llg::SweepIn sw = c->sw;
+    sw.held_samples = n_samples;
+    const llg::MaterialIn mat = c->has_material ? c->mat : llg::MaterialIn{1e-11, 1e5, 0.0, 0.1, 0.0};
+    char err[256];
+    if (!llg::derive(c->b, c->a0, mat, c->sc, sw, &d, err, sizeof err, c->volume)) return fail(LLG_EINVAL, "%s", err);
+    if (d.steps_per_loop != 0) return fail(LLG_EINVAL, "a sample count is set only for a held (constant) field");
+    c->sw.held_samples = n_samples;
+    return LLG_OK;
+}
+
 llg_status llg_set_cell_volume(llg_ctx *c, double volume_m3)
 {
     if (!c) return fail(LLG_EINVAL, "ctx is NULL");
@@ -455,6 +474,11 @@ llg_status llg_set_tuning(llg_ctx *c, int key, int64_t value)
             if (value > (1LL << 22)) return fail(LLG_EINVAL, "at most 4 TB for the adjoint's states");
             c->adjoint_state_mb = value;
             return LLG_OK;
+        case LLG_TUNE_CELLS_PER_THREAD:
+            if (value != 0 && value != 1 && value != 2 && value != 4)
+                return fail(LLG_EINVAL, "cells per thread must be 0 (automatic), 1, 2 or 4");
+            c->tune_cpt = (int)value;
+            return LLG_OK;
         case LLG_TUNE_HANDOFF_TIMEOUT_MS:
             if (value < 1 || value > 3600000) return fail(LLG_EINVAL, "hand-off timeout must be 1 ms .. 1 h");
             c->handoff_timeout_ms = value;
@@ -468,6 +492,24 @@ llg_status llg_set_tuning(llg_ctx *c, int key, int64_t value)
             return LLG_OK;
         default:
             return fail(LLG_EINVAL, "unknown tuning key %d", key);
+    }
+}
+
+llg_status llg_get_tuning(const llg_ctx *c, int key, int64_t *value)
+{
+    if (!c || !value) return fail(LLG_EINVAL, "NULL argument");
+    switch (key) {
+        case LLG_TUNE_ROD_KIND: *value = c->tune_kind; return LLG_OK;
+        case LLG_TUNE_RODS_PER_CTA: *value = c->tune_rods; return LLG_OK;
+        case LLG_TUNE_CHUNK_STEPS: *value = c->chunk_steps; return LLG_OK;
+        case LLG_TUNE_ROWS_PER_THREAD: *value = c->tune_rows; return LLG_OK;
+        case LLG_TUNE_GENERIC_KERNEL: *value = c->tune_generic; return LLG_OK;
+        case LLG_TUNE_BALANCE: *value = c->tune_balance; return LLG_OK;
+        case LLG_TUNE_ADJOINT_STATE_MB: *value = c->adjoint_state_mb; return LLG_OK;
+        case LLG_TUNE_HANDOFF_TIMEOUT_MS: *value = c->handoff_timeout_ms; return LLG_OK;
+        case LLG_TUNE_WITHHOLD_HANDOFF: *value = c->withhold_handoff; return LLG_OK;
+        case LLG_TUNE_CELLS_PER_THREAD: *value = c->tune_cpt; return LLG_OK;
+        default: return fail(LLG_EINVAL, "unknown tuning key %d", key);
     }
 }
 
@@ -531,14 +573,14 @@ llg_status llg_advance(llg_ctx *c, int64_t n_steps, float *m_samples)
             ++c->launches;
         }
     } else if (eng == LLG_ENGINE_STREAM) {
-        const size_t cells = (size_t)c->n_real * (size_t)ncells_of(c);
-        const size_t need = 8 * cells + llg::slab_partial_floats(c->n_real);
+        const size_t padded = llg::slab_state_float4s(kp, c->n_real);
+        const size_t need = 8 * padded + llg::slab_partial_floats(c->n_real);
         s = grow(&c->d_slab, &c->slab_cap, need);
         if (s != LLG_OK) return s;
         float4 *a = reinterpret_cast<float4 *>(c->d_slab);
-        float4 *b = a + cells;
+        float4 *b = a + padded;
         LLG_CUDA(llg::slab_advance(kp, splan, c->d_m, c->n_real, c->step, n_steps, m_samples, c->d_status, a, b,
-                                   c->d_slab + 8 * cells, c->stream, &c->launches),
+                                   c->d_slab + 8 * padded, c->stream, &c->launches),
                  "streaming engine launch");
     } else {
         const size_t per = (size_t)c->n_real * (size_t)ncells_of(c) * 3;
@@ -572,6 +614,7 @@ llg_status llg_sync(llg_ctx *c, double timeout_s)
     if (!c->d_status) return LLG_OK;
     LLG_CUDA(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
     if (st & 2) return fail(LLG_ETIMEOUT, "a resident-engine hand-off wait gave up");
+    if (st & 4) return fail(LLG_ETIMEOUT, "a streaming-engine staging wait gave up");
     if (st) return fail(LLG_ENONFINITE, "a non-finite magnetisation was sampled");
     return LLG_OK;
 }

@@ -4,10 +4,7 @@
 // Two kernels, chosen by rod size:
 //
 //  rod_twophase_kernel  (rods whose state and predictor state both fit: b >= 2 in the paper's
-//      ladder).  Several rods per CTA, each padded with a zero ghost layer so the 6-neighbour
-//      stencil has no branches.  Per step: every thread draws the thermal field of its cells,
-//      computes the predictor into the P buffer and keeps m + dt/2 f(m) and the thermal field in
-//      registers; barrier; the corrector reads P and overwrites M; barrier.
+//      ladder), in k_rod_small.cu.  Several rods per CTA, each padded with a zero ghost layer.
 //
 //  rod_pipelined_kernel (the b = 1 rod, 8x24x56 = 10752 cells: M alone is 129 KB, M and a full
 //      predictor copy do not fit).  One rod per CTA.  Each thread owns rows along x (fixed y, z);
@@ -46,143 +43,6 @@ namespace {
 constexpr int kMaxThreads = 768;
 
 __device__ __forceinline__ float3 zero3() { return make_float3(0.f, 0.f, 0.f); }
-
-// ------------------------------------------------------------------------------------------
-// two-phase kernel
-// ------------------------------------------------------------------------------------------
-// Shared memory: M[tot] and P[tot] float4 (x, y, z, 0), tot = rods_per_cta * (nx+2)(ny+2)(nz+2):
-// each rod padded by a zero ghost layer.
-template <int CPT, bool AX>
-__global__ void __launch_bounds__(kMaxThreads) rod_twophase_kernel(KParams p, float *__restrict__ m_glob,
-                                                            int n_real, int rods_per_cta,
-                                                            long long step0, long long n_steps,
-                                                            float *__restrict__ samples,
-                                                            int *__restrict__ status)
-{
-    extern __shared__ float4 sm4[];
-    const int px = p.nx + 2, py = p.ny + 2;
-    const int sy = px, sz = px * py;
-    const int rod_pad = sz * (p.nz + 2);
-    const int rod0 = blockIdx.x * rods_per_cta;
-    const int nrod = min(rods_per_cta, n_real - rod0);
-    const int tot = rods_per_cta * rod_pad;
-    float4 *M = sm4, *P = sm4 + tot;
-    const int T = blockDim.x;
-    const int ncell = p.ncells;
-    const int cta_cells = nrod * ncell;
-
-    for (int i = threadIdx.x; i < 2 * tot; i += T) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
-    for (int i = threadIdx.x; i < cta_cells; i += T) {
-        const int rod = i / ncell, c = i - rod * ncell;
-        const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
-        const float *g = m_glob + ((size_t)(rod0 + rod) * ncell + c) * 3;
-        M[rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1)] = make_float4(g[0], g[1], g[2], 0.f);
-    }
-
-    int pidx[CPT];
-    uint32_t cell[CPT], real[CPT];
-    bool act[CPT];
-    float3 uax[CPT];  // easy axes (dispersed-axis mode only)
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-        const int i = threadIdx.x + k * T;
-        act[k] = i < cta_cells;
-        const int ii = act[k] ? i : 0;
-        const int rod = ii / ncell, c = ii - rod * ncell;
-        const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
-        pidx[k] = rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1);
-        cell[k] = (uint32_t)c;
-        real[k] = p.real0 + (uint32_t)(rod0 + rod);
-        uax[k] = zero3();
-        if constexpr (AX) {
-            if (act[k]) uax[k] = xyz(__ldg(p.axis + (size_t)(rod0 + rod) * ncell + c));
-        }
-    }
-    __syncthreads();
-
-    Sweep field;
-    field.init(step0, p);
-    float Hn = field.value();
-    const long long se = p.sample_every;
-    long long next_sample = (samples && se > 0) ? (step0 / se + 1) * se : -1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = T >> 5;
-
-    // thermal field of the next step, drawn before the barrier that ends the current one
-    float3 hpre[CPT];
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) hpre[k] = thermal_field(p.seed, real[k], cell[k], (unsigned long long)step0, p.sigma);
-    for (long long s = 0; s < n_steps; ++s) {
-        const unsigned long long n = (unsigned long long)(step0 + s);
-        field.inc();
-        const float Hn1 = field.value();
-        float3 acc[CPT], hth[CPT];
-#pragma unroll
-        for (int k = 0; k < CPT; ++k) {
-            if (!act[k]) continue;
-            const int q = pidx[k];
-            hth[k] = hpre[k];
-            const float3 mi = xyz(M[q]);
-            float3 nb = add3(xyz(M[q - 1]), xyz(M[q + 1]));
-            nb = add3(nb, xyz(M[q - sy]));
-            nb = add3(nb, xyz(M[q + sy]));
-            nb = add3(nb, xyz(M[q - sz]));
-            nb = add3(nb, xyz(M[q + sz]));
-            const float3 H = effective_field_sel<AX>(nb, mi, hth[k], p, Hn, uax[k]);
-            const float3 s0 = llg_torque(mi, H, p.alpha);
-            P[q] = pad4(normalised(axpy(p.neg_dt_g1, s0, mi)));
-            acc[k] = axpy(p.neg_hdt_g1, s0, mi);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < CPT; ++k) {
-            if (!act[k]) continue;
-            const int q = pidx[k];
-            const float3 ti = xyz(P[q]);
-            float3 nb = add3(xyz(P[q - 1]), xyz(P[q + 1]));
-            nb = add3(nb, xyz(P[q - sy]));
-            nb = add3(nb, xyz(P[q + sy]));
-            nb = add3(nb, xyz(P[q - sz]));
-            nb = add3(nb, xyz(P[q + sz]));
-            const float3 H = effective_field_sel<AX>(nb, ti, hth[k], p, Hn1, uax[k]);
-            const float3 s1 = llg_torque(ti, H, p.alpha);
-            M[q] = pad4(normalised(axpy(p.neg_hdt_g1, s1, acc[k])));
-            hpre[k] = thermal_field(p.seed, real[k], cell[k], n + 1, p.sigma);
-        }
-        __syncthreads();
-        Hn = Hn1;
-        if ((long long)n + 1 == next_sample) {
-            // M now holds the state after step n; the next phase only reads M until the
-            // barrier that precedes its next write, so no extra barrier is needed here.
-            const long long k = next_sample / se;
-            if (k < p.n_samples) {
-                for (int rod = warp; rod < nrod; rod += nwarps) {
-                    float part = 0.f;
-                    for (int c = lane; c < ncell; c += 32) {
-                        const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
-                        part += M[rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1)].z;
-                    }
-                    const float mean = warp_cell_mean(part, ncell);
-                    if (lane == 0) {
-                        samples[(size_t)(rod0 + rod) * p.n_samples + k] = mean;
-                        if (!isfinite(mean)) atomicOr(status, 1);
-                    }
-                }
-            }
-            next_sample += se;
-        }
-    }
-
-    for (int i = threadIdx.x; i < cta_cells; i += T) {
-        const int rod = i / ncell, c = i - rod * ncell;
-        const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
-        const float4 v = M[rod * rod_pad + (x + 1) + sy * (y + 1) + sz * (z + 1)];
-        float *g = m_glob + ((size_t)(rod0 + rod) * ncell + c) * 3;
-        g[0] = v.x;
-        g[1] = v.y;
-        g[2] = v.z;
-    }
-}
 
 // ------------------------------------------------------------------------------------------
 // plane-pipelined kernel
@@ -636,7 +496,7 @@ struct HandoffCtl {
 template <int R, int NX, int NY = 0, int NZ = 0, int SHAPE = -1, bool AX = false>
 __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_kernel(
     KParams p, float *__restrict__ m_glob, long long step0, int n_steps, int n_real, float *__restrict__ samples,
-    int *__restrict__ status, unsigned *__restrict__ flags, int balanced, HandoffCtl hc)
+    int *__restrict__ status, unsigned *__restrict__ flags, int balanced, long long slice, HandoffCtl hc)
 {
     static_assert(NX >= 3 && NX % 2 == 0, "merged schedule with even plane count");
     extern __shared__ float4 sm4[];
@@ -644,42 +504,38 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_
     for (int i = threadIdx.x; i < (NX + 2) * PL; i += blockDim.x) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     PipelinedRod<R, NX, NY, NZ, SHAPE, AX> w;
     w.setup(sm4, p);
-    __syncthreads();
-    __shared__ int go;
-    if (!balanced) {
-        w.run(p, m_glob, blockIdx.x, step0, n_steps, samples, status);
-        return;
-    }
-    const long long N = n_steps;
-    const long long W = (long long)n_real * N;
-    const long long C = (W + gridDim.x - 1) / gridDim.x;
+    // The segments of this CTA's slice, walked by every thread from uniform values only (the
+    // launch parameters and blockIdx), so the rod index -- and the Philox round keys run()
+    // derives from it -- stay warp-uniform; no 64-bit division (a called routine here): the
+    // host passes the slice length and the first rod is found by a walk over rods.  Without
+    // balancing the slice is rod blockIdx.x.  kind 1: the rod's first steps (then release
+    // flags[rod]); kind 2: its last steps (after waiting for flags[rod]; a wait that runs out
+    // sets status bit 1 and the CTA goes on, the result then being flagged); kind 0: all of it.
+    const long long N = n_steps, W = (long long)n_real * N;
+    const long long C = balanced ? slice : N;
     const long long lo = min((long long)blockIdx.x * C, W), hi = min(lo + C, W);
-    for (long long pos = lo; pos < hi;) {
-        const int rod = (int)(pos / N);
+    int rod = balanced ? 0 : (int)blockIdx.x;
+    while ((long long)(rod + 1) * N <= lo) ++rod;
+    for (long long pos = lo; pos < hi; ++rod) {
         const long long off = pos - (long long)rod * N;
         const long long len = min(hi, (long long)(rod + 1) * N) - pos;
-        // kind 1: the rod's first len steps; kind 2: its last len steps; kind 0: all of it
         const int kind = off != 0 ? 1 : (len < N ? 2 : 0);
         pos += len;
         if (kind == 2) {
             if (threadIdx.x == 0) {
                 const unsigned long long t0 = globaltimer_ns();
-                int ok = 1;
                 while (ld_acquire_gpu(flags + rod) == 0u) {
                     if (globaltimer_ns() - t0 > hc.timeout_ns) {
-                        ok = 0;
                         atomicOr(status, 2);
                         break;
                     }
                     __nanosleep(200);
                 }
                 __threadfence();
-                go = ok;
             }
             __syncthreads();
-            if (!go) break;
         }
-        w.run(p, m_glob, rod, step0 + (kind == 2 ? N - len : 0), len, samples, status);
+        w.run(p, m_glob, rod, step0 + (kind == 2 ? N - len : 0), (int)len, samples, status);
         if (kind == 1 && threadIdx.x == 0 && !hc.withhold) {
             __threadfence();
             st_release_gpu(flags + rod, 1u);
@@ -725,7 +581,7 @@ int pipelined_threads(int rows, int R)
 }  // namespace
 
 bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_kind, int force_rods,
-              int force_rows)
+              int force_rows, int force_cpt)
 {
     int smem_optin = 0, nsm = 0;
     if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
@@ -744,19 +600,24 @@ bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_ki
     int kind = force_kind;
     if (kind == 0) kind = (p.ncells <= kMaxThreads && twophase_fits) ? 1 : (pipelined_fits ? 2 : 1);
     if (kind == 1) {
-        if (!twophase_fits) return false;
-        const int cpt = p.ncells <= kMaxThreads ? 1 : (p.ncells <= 2 * kMaxThreads ? 2 : 4);
-        const int by_threads = std::max(1, kMaxThreads * cpt / p.ncells);
+        if (!twophase_fits || p.sample_every >= (1LL << 31)) return false;
+        // cells per thread: forced, or the fewest that hold one rod in one CTA
+        int cpt = force_cpt;
+        if (cpt == 0) {
+            cpt = 4;
+            for (int c : {2, 1})
+                if (round_warp((p.ncells + c - 1) / c) <= twophase_max_threads(p, c)) cpt = c;
+        }
+        if (cpt != 1 && cpt != 2 && cpt != 4) return false;
+        const int maxt = twophase_max_threads(p, cpt);
         const int by_smem = (int)std::max<size_t>(1, (size_t)smem_optin / rod_bytes);
         int rods = 1;
-        if (force_rods > 0) {
-            if (force_rods > by_threads || force_rods > by_smem) return false;
-            rods = force_rods;
-        }
+        if (force_rods > 0) rods = force_rods;
+        if (rods > by_smem || round_warp((rods * p.ncells + cpt - 1) / cpt) > maxt) return false;
         plan->kind = 1;
         plan->rods_per_cta = rods;
         plan->cells_per_thread = cpt;
-        plan->threads = std::min(kMaxThreads, round_warp((rods * p.ncells + cpt - 1) / cpt));
+        plan->threads = round_warp((rods * p.ncells + cpt - 1) / cpt);
         plan->rows_per_thread = 0;
         plan->smem_bytes = rods * rod_bytes;
         plan->ctas = (n_real + rods - 1) / rods;
@@ -804,15 +665,17 @@ static cudaError_t launch_nx(const KParams &p, const RodPlan &plan, float *m, in
     const int resident = nsm * per_sm;
     int ns = (int)n_steps;  // rod_advance splits longer runs
     HandoffCtl hc{plan.handoff_timeout_ns, plan.withhold_handoff ? 1 : 0};
+    // balance when the rods do not fill whole waves
     if (plan.balance && flags && resident > 0 && n_real > resident && n_real % resident != 0) {
         if ((e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)n_real, st)) != cudaSuccess) return e;
         int balanced = 1;
+        long long slice = ((long long)n_real * ns + resident - 1) / resident;  // rod-steps per CTA
         void *args[] = {(void *)&p, (void *)&m, (void *)&step0, (void *)&ns, (void *)&n_real, (void *)&samples,
-                        (void *)&status, (void *)&flags, (void *)&balanced, (void *)&hc};
+                        (void *)&status, (void *)&flags, (void *)&balanced, (void *)&slice, (void *)&hc};
         return cudaLaunchCooperativeKernel((const void *)kern, dim3(resident), dim3(plan.threads), args,
                                            plan.smem_bytes, st);
     }
-    kern<<<n_real, plan.threads, plan.smem_bytes, st>>>(p, m, step0, ns, n_real, samples, status, flags, 0, hc);
+    kern<<<n_real, plan.threads, plan.smem_bytes, st>>>(p, m, step0, ns, n_real, samples, status, flags, 0, 0LL, hc);
     return cudaGetLastError();
 }
 
@@ -835,28 +698,8 @@ cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_r
     }
     cudaError_t e = cudaSuccess;
     if (plan.kind == 1) {
-#define LLG_TWOPHASE(C)                                                                         \
-    case C:                                                                                     \
-        if (p.axis) {                                                                           \
-            e = set_smem(rod_twophase_kernel<C, true>, plan.smem_bytes);                        \
-            if (e != cudaSuccess) return e;                                                     \
-            rod_twophase_kernel<C, true><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(     \
-                p, m, n_real, plan.rods_per_cta, step0, n_steps, samples, status);              \
-        } else {                                                                                \
-            e = set_smem(rod_twophase_kernel<C, false>, plan.smem_bytes);                       \
-            if (e != cudaSuccess) return e;                                                     \
-            rod_twophase_kernel<C, false><<<plan.ctas, plan.threads, plan.smem_bytes, st>>>(    \
-                p, m, n_real, plan.rods_per_cta, step0, n_steps, samples, status);              \
-        }                                                                                       \
-        break;
-        switch (plan.cells_per_thread) {
-            LLG_TWOPHASE(1)
-            LLG_TWOPHASE(2)
-            LLG_TWOPHASE(4)
-            default:
-                return cudaErrorInvalidValue;
-        }
-#undef LLG_TWOPHASE
+        e = twophase_advance(p, plan, m, n_real, step0, (int)n_steps, samples, status, st);
+        if (e != cudaSuccess) return e;
     } else if (plan.kind == 2 && p.axis && plan.rows_per_thread == 3 && p.nx == 8 && p.ny == 24 && p.nz == 56 &&
                !plan.generic) {
         // the b = 1 rod with dispersed axes: the shape-specialised kernel's axis instance

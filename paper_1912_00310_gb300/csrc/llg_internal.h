@@ -68,6 +68,7 @@ struct ScalingIn {
 struct SweepIn {
     double H_start_Oe, H_turn_Oe, rate_Oe_per_ns, dt, sample_dH_Oe;
     int shape;
+    long long held_samples = 1;  // sample columns of a held (constant) field
 };
 // volume_m3 > 0 overrides the cell volume (b a0)^3 of the thermal field (a single block whose
 // volume is not a cube of the cell edge).
@@ -119,7 +120,13 @@ struct RodPlan {
 // resident kernel can hold the rod.
 // force_kind / force_rods: 0 = automatic.
 bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_kind = 0,
-              int force_rods = 0, int force_rows = 0);
+              int force_rods = 0, int force_rows = 0, int force_cpt = 0);
+// Two-phase kernel (k_rod_small.cu): whether the grid and sweep have a compile-time instance,
+// the largest CTA for cpt cells per thread, and the launch of n_steps (< 2^31) steps.
+bool twophase_shaped(const KParams &p);
+int twophase_max_threads(const KParams &p, int cpt);
+cudaError_t twophase_advance(const KParams &p, const RodPlan &plan, float *m, int n_real, long long step0,
+                             int n_steps, float *samples, int *status, cudaStream_t st);
 // flags: n_real words of device scratch for the balanced schedule's hand-offs (may be NULL:
 // then no balancing).  status bit 0: non-finite sample; bit 1: a hand-off wait gave up.
 cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_real,
@@ -132,7 +139,10 @@ struct SlabPlan {
     size_t smem_bytes;
 };
 bool slab_plan(const KParams &p, int dev, SlabPlan *plan);
-// buf_a, buf_b: n_real * ncells float4 each; partial: slab_partial_floats(n_real) floats.
+// buf_a, buf_b: slab_state_float4s(p, n_real) float4 each (the padded layout
+// [n_real][nz][ny + 4][nx + 4]); partial: slab_partial_floats(n_real) floats.
+// status bit 2 (value 4): a staging wait of the streaming kernel gave up.
+size_t slab_state_float4s(const KParams &p, int n_real);
 cudaError_t slab_advance(const KParams &p, const SlabPlan &plan, float *m, int n_real, long long step0,
                          long long n_steps, float *samples, int *status, float4 *buf_a, float4 *buf_b,
                          float *partial, cudaStream_t st, long long *launches);
@@ -178,8 +188,9 @@ struct CtxView {
     unsigned *d_flags;
     long long step, steps_per_loop;
     KParams kp;  // with the ensemble's seed and real0
-    int tune_kind, tune_rods, tune_rows;
+    int tune_kind, tune_rods, tune_rows, tune_cpt;
     bool tune_generic;
+    long long chunk_steps;  // steps per launch
 };
 llg_status ctx_view(llg_ctx *ctx, CtxView *out);
 void ctx_add_steps(llg_ctx *ctx, long long n);

@@ -1,6 +1,7 @@
 // scaling.cpp -- host FP64 parameter setup of one job: the coarse-graining map (Eqs. 8-13), the
 // coefficients of Eq. 1 and of the Brown thermal field, the triangle and sinusoidal field sweeps and
 // the numerical Grinstein-Koch flow (Eqs. 4-7).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -112,7 +113,7 @@ bool derive(int b, double a0, const MaterialIn &mat, const ScalingIn &sc, const 
         d->sample_every = whole_steps(sw.sample_dH_Oe);
         if (d->sample_every <= 0) d->sample_every = 1;
         d->steps_per_loop = 0;
-        d->n_samples = 1;
+        d->n_samples = std::max(1LL, sw.held_samples);  // sample k after step k * sample_every
     }
     // Eq. 11 (mode 1) or Eq. 13 (mode 2) rescale of m back to the unscaled system
     d->m_rescale = sc.mode == 1 ? d->zeta : (sc.mode == 2 ? sc.delta * d->zeta + (1.0 - sc.delta) : 1.0);

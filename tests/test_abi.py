@@ -192,3 +192,18 @@ def test_loop_stats_from_sums_equal_host_statistics(pkg):
     d = st.as_dict()
     for key in ("Hc_Oe", "Hc_se_Oe", "area_Oe", "area_se_Oe"):
         assert d[key] == pytest.approx(ref[key], rel=1e-10), key
+
+
+def test_level_temperature_and_held_samples(pkg, orc):
+    """T(b) = T0 / (b zeta(b, T0)) (Eq. 12) from the library's map equals the oracle's closed
+    form; T(1) = T0; a held field takes a sample count, a swept one refuses it."""
+    from paper_1912_00310_gb300 import equilibrium as E
+    from workloads import MAGNETITE as M
+    assert E.level_temperature(1) == pytest.approx(310.0, rel=1e-15)
+    for b in (2, 4, 8):
+        assert E.level_temperature(b) == pytest.approx(310.0 / (b * orc.zeta(b, 310.0, M["Tc"])), rel=1e-12)
+    g = E.make_grid(4, 310.0, sample_every=50)
+    assert g.n_samples == 1
+    g.set_held_samples(21)
+    assert g.n_samples == 21 and g.sample_every == 50
+    g.close()

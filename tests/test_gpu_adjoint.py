@@ -91,9 +91,11 @@ def test_adjoint_matches_fp64_central_differences(pkg, orc):
 
 
 def test_adjoint_matches_central_differences(pkg):
-    """Central differences of the GPU forward loss (same noise at +-h), FP32, h = 1e-2: a check
-    of the whole GPU path on its own; FP32 rounding of the forward loss limits the difference
-    quotient, so the bar is looser than against the FP64 differences above."""
+    """Central differences of the GPU forward loss (same noise at +-h), FP32, h = 1e-2: the whole
+    GPU path on its own, within 1e-2 relative with no absolute floor.  On this case the FP32
+    difference quotient agrees with the adjoint to 3e-3 at h = 1e-2 (truncation) and to 3e-4 at
+    h = 3e-3; below h = 1e-3 FP32 rounding of the forward loss dominates (1.5e-2 on the smallest
+    component, dL/ds_K)."""
     dims, n_real, n_steps = ROD_DIMS[4], 8, 3000
     g = grid(pkg, dims)
     target = target_for(g)
@@ -110,7 +112,7 @@ def test_adjoint_matches_central_differences(pkg):
             g.reset(seed=4, n_real=n_real)
             vals.append(g.loss_grad(n_steps, target, 0, 256)[0])
         fd = (vals[0] - vals[1]) / (2 * h)
-        assert grad[k] == pytest.approx(fd, rel=3e-2, abs=1e-2 * np.abs(grad).max()), (k, grad[k], fd)
+        assert grad[k] == pytest.approx(fd, rel=1e-2), (k, grad[k], fd)
         g.set_scaling(mode=1, Tc=M["Tc"], scale=tuple(base))
     g.close()
 

@@ -373,3 +373,37 @@ def test_twophase_variants_bitwise_with_plain(pkg, dims, rods, disp):
         g.close()
     assert torch.equal(outs[0], outs[1])
     assert float((torch.linalg.norm(outs[0], dim=-1) - 1).abs().max()) < 1e-6
+
+
+def test_held_field_samples_and_time_average(pkg, orc):
+    """A held (zero) field with sample columns (the equilibrium runs behind Eq. 12): the b = 8 rod
+    at 310 K, 64 realisations, 20k steps sampled every 100: the early samples equal the oracle's
+    within 1e-4 (trajectory parity), and the time average of |m_z| after the burn-in lies within
+    three combined standard errors of the oracle's."""
+    from paper_1912_00310_gb300 import equilibrium as E
+    n_real, steps, every = 64, 20000, 100
+    g = E.make_grid(8, 310.0, sample_every=every)
+    g.set_held_samples(steps // every + 1)
+    assert g.n_samples == steps // every + 1 and g.steps_per_loop == 0
+    g.reset(seed=5, n_real=n_real)
+    S = torch.zeros((n_real, g.n_samples), device="cuda")
+    g.advance(steps, S)
+    g.sync(120)
+    gs = S.double().cpu().numpy()[:, 1:]
+    p = orc.material_problem(1, 3, 7, a0=M["a0"], b=8, A0=M["A0"], K0=M["K0"], Ms=M["Ms"], alpha=M["alpha"],
+                             T=310.0, dt=20e-15, mode=1, Tc=M["Tc"], H_start_Oe=0.0, H_turn_Oe=0.0,
+                             rate_Oe_per_ns=0.0)
+    ref = orc.uniform_state(n_real, 21)
+    rs, _ = orc.run(p, ref, seed=5, n_steps=steps, sample_every=every, n_samples=g.n_samples)
+    rs = rs[:, 1:]
+    assert np.abs(gs[:, :5] - rs[:, :5]).max() <= 1e-4  # 500 steps
+    k0 = 50  # burn-in: the first 5000 steps
+    a, b = np.abs(gs[:, k0:]).mean(1), np.abs(rs[:, k0:]).mean(1)
+    se = math.hypot(a.std(ddof=1), b.std(ddof=1)) / math.sqrt(n_real)
+    assert abs(a.mean() - b.mean()) <= 3 * se, (a.mean(), b.mean(), se)
+    assert 0.3 < a.mean() < 1.0
+    with pytest.raises(pkg.LLGError):
+        swept = E.make_grid(8, 310.0)
+        swept.set_sweep(H_start=100.0, H_turn=-100.0, rate=1000.0, dt=20e-15, sample_dH=1.0)
+        swept.set_held_samples(10)
+    g.close()
