@@ -53,7 +53,8 @@ def parse():
                          "graph calls and print one JSON line (ci: without the b = 1 jobs at "
                          "10 Oe/ns); not part of the default benchmark")
     ap.add_argument("--profile-case", default=None,
-                    help="run a small untimed case for a profiler (b1, b1-plain, b4) and exit")
+                    help="run a small untimed case for a profiler (b1, b1-plain, b4, b4-rows, slab, "
+                         "adjoint) and exit")
     return ap.parse_args()
 
 
@@ -661,6 +662,14 @@ def adjoint_calibration(args, torch, pkg):
     for _ in range(n_eval):
         L, grad = g.loss_grad(c5["window_steps"], tgt, 0, c5["ckpt_every"])
     t_grad = (time.perf_counter() - t0) / n_eval
+    # the forward-mode method on the same workload (one pass carrying the three tangents)
+    g.set_tuning(pkg.TUNE_GRAD_METHOD, 1)
+    Lt, gt = g.loss_grad(c5["window_steps"], tgt, 0, c5["ckpt_every"])  # warm-up
+    t0 = time.perf_counter()
+    for _ in range(n_eval):
+        Lt, gt = g.loss_grad(c5["window_steps"], tgt, 0, c5["ckpt_every"])
+    t_tan = (time.perf_counter() - t0) / n_eval
+    g.set_tuning(pkg.TUNE_GRAD_METHOD, 0)
     S = torch.zeros((c5["n_real"], g.n_samples), device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -670,6 +679,10 @@ def adjoint_calibration(args, torch, pkg):
     g.close()
     return {"grads_per_s": 1.0 / t_grad, "s_per_grad": t_grad, "forward_only_s": t_fwd,
             "grad_over_forward": t_grad / t_fwd, "loss": L, "grad": [float(x) for x in grad],
+            "method": "reverse-mode adjoint, checkpoints every ckpt_every steps",
+            "tangent": {"grads_per_s": 1.0 / t_tan, "s_per_grad": t_tan, "grad_over_forward": t_tan / t_fwd,
+                        "loss": Lt, "grad": [float(x) for x in gt],
+                        "max_rel_diff_vs_adjoint": float(max(abs(a - b) / abs(a) for a, b in zip(grad, gt)))},
             "cell_steps_per_grad": c5["n_real"] * math.prod(c5["dims"]) * c5["window_steps"],
             "timing": "host wall clock per synchronous llg_loop_area_grad call"}
 
@@ -687,8 +700,12 @@ def profile_case(name):
         cfg = dict(CONFIGS["rod_b1_256real"])
         n_real, steps = 160, (200 if name == "b1" else 5)
         eng = pkg.ENGINE_RESIDENT if name == "b1" else pkg.ENGINE_PLAIN
+    elif name == "b4-rows":
+        # 608 b = 4 rods with the row kernel's default shape (one rod per CTA), no autotuning
+        cfg = dict(CONFIGS["rod_b4_4real"])
+        n_real, steps, eng = 608, 2000, pkg.ENGINE_RESIDENT
     elif name == "b4":
-        # 608 b = 4 rods with the autotuned two-phase launch shape
+        # 608 b = 4 rods with the autotuned launch shape
         cfg = dict(CONFIGS["rod_b4_4real"])
         n_real, steps, eng = 608, 2000, pkg.ENGINE_RESIDENT
     elif name == "slab":

@@ -166,8 +166,9 @@ llg_status llg_gk_flow(double Tstar0, double h0, double g0, double b, int64_t n_
 llg_status llg_set_engine(llg_ctx *ctx, int engine);
 
 /* Launch-shape overrides of the resident engine (0 = automatic, the default):
- *   LLG_TUNE_ROD_KIND      1 two-phase kernel, 2 plane-pipelined kernel
- *   LLG_TUNE_RODS_PER_CTA  rods per CTA of the two-phase kernel
+ *   LLG_TUNE_ROD_KIND      1 two-phase kernel, 2 plane-pipelined kernel, 3 row kernel (the
+ *                          b = 2, 4, 8 rods of the paper's ladder: a thread per x-row)
+ *   LLG_TUNE_RODS_PER_CTA  rods per CTA of the two-phase and row kernels
  *   LLG_TUNE_CHUNK_STEPS   Heun steps per launch (default 2^20; llg_autotune sets it so the
  *                          launch overhead stays near 1% of a launch)
  *   LLG_TUNE_ROWS_PER_THREAD  rows per thread of the plane-pipelined kernel (1..4)
@@ -180,11 +181,17 @@ llg_status llg_set_engine(llg_ctx *ctx, int engine);
  *                             step); within it every checkpoint segment is recomputed in one
  *                             launch and the window reversed in another, beyond it (or with 0)
  *                             segment by segment.  The states, and so the loss, are the same
- *                             either way; the gradient's partial sums are grouped differently
- *                             (to about 1e-7 relative).
+ *                             either way; the gradient's FP32 partial sums may be grouped
+ *                             differently where a segment boundary splits a 64-step block
+ *                             (measured: bitwise equal with aligned segments; FP32 blocks differ
+ *                             from a per-step FP64 accumulation by at most 2e-8 relative).
  *   LLG_TUNE_CELLS_PER_THREAD cells per thread of the two-phase kernel (0 automatic, 1, 2, 4;
  *                             the b = 4 and b = 8 rods get 768 / cells-per-thread threads per CTA
  *                             at most, other grids 768)
+ *   LLG_TUNE_GRAD_METHOD      llg_loop_area_grad's method: 0 the reverse-mode adjoint (default),
+ *                             1 forward-mode tangents (one pass carrying dm/d(s_K, s_alpha, s_Ms);
+ *                             no checkpoints or stored window; the same loss and, to FP32
+ *                             rounding, the same gradient)
  *   LLG_TUNE_HANDOFF_TIMEOUT_MS  longest wait (ms, default 30000, 1 .. 3600000) of a CTA of the
  *                             balanced schedule for the CTA that runs the first part of a rod it
  *                             finishes; on expiry the CTA skips its remaining segments, and the
@@ -204,6 +211,7 @@ llg_status llg_set_engine(llg_ctx *ctx, int engine);
 #define LLG_TUNE_HANDOFF_TIMEOUT_MS 8
 #define LLG_TUNE_WITHHOLD_HANDOFF 9
 #define LLG_TUNE_CELLS_PER_THREAD 10
+#define LLG_TUNE_GRAD_METHOD 11
 llg_status llg_set_tuning(llg_ctx *ctx, int key, int64_t value);
 
 /* The current value of a tuning key (as set, by llg_set_tuning or llg_autotune; 0 = automatic).
@@ -287,11 +295,13 @@ llg_status llg_autotune(llg_ctx *ctx, int64_t trial_steps, double *best_rate);
  *                sample number (length llg_num_samples)
  *   objective 1: L = sum_k (mbar_k + mbar_k+1)/2 (H_k+1 - H_k), the signed area under the
  *                window's mean loop (target unused)
- * Method: a forward pass with the resident engine storing the state every ckpt_every steps,
- * then, segment by segment from the last, a kernel that recomputes the segment's states from its
- * checkpoint and runs the reverse-mode adjoint of the Heun step back through them (one CTA per
- * realisation; rods of at most 1024 cells with free faces).  Allocates its scratch (states of
- * one segment and the checkpoints) for the duration of the call; synchronises.
+ * Method (LLG_TUNE_GRAD_METHOD 0, the default): a forward pass with the resident engine storing
+ * the state every ckpt_every steps, then, segment by segment from the last, a kernel that
+ * recomputes the segment's states from its checkpoint and runs the reverse-mode adjoint of the
+ * Heun step back through them (one CTA per realisation; rods of at most 1024 cells with free
+ * faces).  Method 1: one forward pass carrying the tangents dm/d(s_K, s_alpha, s_Ms) beside the
+ * state (ckpt_every unused).  Either allocates its scratch for the duration of the call and
+ * synchronises.
  * loss_out (optional) receives L; grad_out receives dL/d(s_K, s_alpha, s_Ms).
  * Errors: EINVAL (no ensemble, no sample in the window, window past the loop end),
  * EUNSUPPORTED (grid), ENOMEM, ECUDA. */

@@ -13,13 +13,13 @@ from . import _lib
 from ._lib import (COEFF_NAMES, ENGINE_AUTO, ENGINE_PLAIN, ENGINE_RESIDENT, ENGINE_STREAM,
                    TUNE_ADJOINT_STATE_MB, TUNE_BALANCE, TUNE_CHUNK_STEPS, TUNE_GENERIC_KERNEL,
                    TUNE_HANDOFF_TIMEOUT_MS, TUNE_ROD_KIND, TUNE_RODS_PER_CTA, TUNE_ROWS_PER_THREAD,
-                   TUNE_WITHHOLD_HANDOFF, TUNE_CELLS_PER_THREAD, LLGError, LoopStats)
+                   TUNE_WITHHOLD_HANDOFF, TUNE_CELLS_PER_THREAD, TUNE_GRAD_METHOD, LLGError, LoopStats)
 
 __all__ = ["Grid", "run_batch", "loop_loss", "LLGError", "LoopStats", "loop_stats", "gk_flow",
            "specific_loss_power", "measure_alu_peak", "ENGINE_AUTO", "ENGINE_RESIDENT",
            "ENGINE_PLAIN", "ENGINE_STREAM", "TUNE_ROD_KIND", "TUNE_RODS_PER_CTA", "TUNE_CHUNK_STEPS",
            "TUNE_ROWS_PER_THREAD", "TUNE_GENERIC_KERNEL", "TUNE_BALANCE", "TUNE_ADJOINT_STATE_MB",
-           "TUNE_HANDOFF_TIMEOUT_MS", "TUNE_WITHHOLD_HANDOFF", "TUNE_CELLS_PER_THREAD", "library"]
+           "TUNE_HANDOFF_TIMEOUT_MS", "TUNE_WITHHOLD_HANDOFF", "TUNE_CELLS_PER_THREAD", "TUNE_GRAD_METHOD", "library"]
 
 
 def library():

@@ -21,7 +21,7 @@ STATUS = {0: "LLG_OK", 1: "LLG_EINVAL", 2: "LLG_ENOMEM", 3: "LLG_ECUDA", 4: "LLG
 ENGINE_AUTO, ENGINE_RESIDENT, ENGINE_PLAIN, ENGINE_STREAM = 0, 1, 2, 3
 TUNE_ROD_KIND, TUNE_RODS_PER_CTA, TUNE_CHUNK_STEPS, TUNE_ROWS_PER_THREAD = 1, 2, 3, 4
 TUNE_GENERIC_KERNEL, TUNE_BALANCE, TUNE_ADJOINT_STATE_MB = 5, 6, 7
-TUNE_HANDOFF_TIMEOUT_MS, TUNE_WITHHOLD_HANDOFF, TUNE_CELLS_PER_THREAD = 8, 9, 10
+TUNE_HANDOFF_TIMEOUT_MS, TUNE_WITHHOLD_HANDOFF, TUNE_CELLS_PER_THREAD, TUNE_GRAD_METHOD = 8, 9, 10, 11
 
 
 class LoopStats(C.Structure):

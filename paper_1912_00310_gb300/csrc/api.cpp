@@ -34,6 +34,7 @@ struct llg_ctx {
     int engine = LLG_ENGINE_AUTO;
     int tune_kind = 0, tune_rods = 0, tune_rows = 0, tune_generic = 0, tune_balance = 1, tune_cpt = 0;
     long long adjoint_state_mb = 16384;  // budget for the adjoint's stored window states
+    int grad_method = 0;                 // 0 reverse-mode adjoint, 1 forward-mode tangents
     long long chunk_steps = 1LL << 20;
     long long handoff_timeout_ms = 30000;  // balanced resident schedule: longest hand-off wait
     int withhold_handoff = 0;              // test hook: the hand-offs are never released
@@ -453,7 +454,7 @@ llg_status llg_set_tuning(llg_ctx *c, int key, int64_t value)
     if (value < 0) return fail(LLG_EINVAL, "tuning values must be >= 0");
     switch (key) {
         case LLG_TUNE_ROD_KIND:
-            if (value > 2) return fail(LLG_EINVAL, "rod kernel kind must be 0, 1 or 2");
+            if (value > 3) return fail(LLG_EINVAL, "rod kernel kind must be 0, 1, 2 or 3");
             c->tune_kind = (int)value;
             return LLG_OK;
         case LLG_TUNE_RODS_PER_CTA:
@@ -478,6 +479,10 @@ llg_status llg_set_tuning(llg_ctx *c, int key, int64_t value)
             if (value != 0 && value != 1 && value != 2 && value != 4)
                 return fail(LLG_EINVAL, "cells per thread must be 0 (automatic), 1, 2 or 4");
             c->tune_cpt = (int)value;
+            return LLG_OK;
+        case LLG_TUNE_GRAD_METHOD:
+            if (value > 1) return fail(LLG_EINVAL, "gradient method must be 0 (adjoint) or 1 (tangent)");
+            c->grad_method = (int)value;
             return LLG_OK;
         case LLG_TUNE_HANDOFF_TIMEOUT_MS:
             if (value < 1 || value > 3600000) return fail(LLG_EINVAL, "hand-off timeout must be 1 ms .. 1 h");
@@ -509,6 +514,7 @@ llg_status llg_get_tuning(const llg_ctx *c, int key, int64_t *value)
         case LLG_TUNE_HANDOFF_TIMEOUT_MS: *value = c->handoff_timeout_ms; return LLG_OK;
         case LLG_TUNE_WITHHOLD_HANDOFF: *value = c->withhold_handoff; return LLG_OK;
         case LLG_TUNE_CELLS_PER_THREAD: *value = c->tune_cpt; return LLG_OK;
+        case LLG_TUNE_GRAD_METHOD: *value = c->grad_method; return LLG_OK;
         default: return fail(LLG_EINVAL, "unknown tuning key %d", key);
     }
 }
@@ -699,6 +705,94 @@ llg_status llg_set_state(llg_ctx *c, const float *m, int64_t step)
     return LLG_OK;
 }
 
+// Loss of the window's mean loop and its weights dL/dmbar_k (objective 0: mismatch against
+// target; 1: signed trapezoid area), from the realisation means mbar of samples k_first ...
+static double window_loss(const llg::Derived &d, const llg::SweepIn &sw, int objective, const double *target,
+                          long long k_first, long long K, const std::vector<double> &mbar, std::vector<double> &wk)
+{
+    const long long se = d.sample_every;
+    std::vector<double> Hk((size_t)K);
+    for (long long k = 0; k < K; ++k) Hk[(size_t)k] = llg::field_Oe(d, sw, (k_first + k) * se);
+    wk.assign((size_t)K, 0.0);
+    double L = 0.0;
+    if (objective == 0) {
+        for (long long k = 0; k < K; ++k) {
+            const double err = mbar[(size_t)k] - target[k_first + k];
+            L += err * err / (double)K;
+            wk[(size_t)k] = 2.0 * err / (double)K;
+        }
+    } else {
+        for (long long k = 0; k + 1 < K; ++k) {
+            const double dH = Hk[(size_t)k + 1] - Hk[(size_t)k];
+            L += 0.5 * (mbar[(size_t)k] + mbar[(size_t)k + 1]) * dH;
+            wk[(size_t)k] += 0.5 * dH;
+            wk[(size_t)k + 1] += 0.5 * dH;
+        }
+    }
+    return L;
+}
+
+// The forward-mode method: one pass carrying dm/d(s_K, s_alpha, s_Ms) (k_tangent.cu), the
+// derivatives of the simulation coefficients taken here in FP64.
+static llg_status tangent_grad(llg_ctx *c, const llg::Derived &d, const llg::KParams &kp, long long N, int objective,
+                               const double *target, long long k_first, long long K, size_t state, double *loss_out,
+                               double grad_out[3])
+{
+    if (!llg::tangent_supported(kp, c->device))
+        return fail(LLG_EUNSUPPORTED, "the tangent method handles rods of at most 1024 cells with free faces");
+    if (K > 0x7fffffffLL) return fail(LLG_EINVAL, "too many samples in the window");
+    const double sK = c->sc.sK, sA = c->sc.sAlpha, sM = c->sc.sMs;
+    const double alpha = d.alpha, a = c->sw.dt * d.g1;
+    const double dcoef[15] = {0.0, 0.0, -d.c_ex / sM,                                  // c_ex
+                              d.c_an / sK, 0.0, -d.c_an / sM,                          // c_an
+                              0.0, alpha / sA, 0.0,                                    // alpha
+                              0.0, -2.0 * alpha * a / (1.0 + alpha * alpha) * alpha / sA, 0.0,  // a
+                              0.0, 0.5 / sA, -0.5 / sM};                               // dsigma / sigma
+    float *work = nullptr, *smp = nullptr, *dsmp = nullptr;
+    cudaError_t e = cudaMalloc(&work, sizeof(float) * state);
+    if (e == cudaSuccess) e = cudaMalloc(&smp, sizeof(float) * (size_t)c->n_real * (size_t)K);
+    if (e == cudaSuccess) e = cudaMalloc(&dsmp, sizeof(float) * 3 * (size_t)c->n_real * (size_t)K);
+    auto cleanup = [&]() {
+        cudaFree(work);
+        cudaFree(smp);
+        cudaFree(dsmp);
+    };
+    if (e != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return fail(LLG_ENOMEM, "tangent buffers: %s", cudaGetErrorString(e));
+    }
+    const cudaStream_t st = c->stream;
+    std::vector<float> hs((size_t)c->n_real * (size_t)K), hd(3 * hs.size());
+    e = cudaMemcpyAsync(work, c->d_m, sizeof(float) * state, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = llg::tangent_forward(kp, dcoef, c->n_real, c->step, N, k_first, (int)K, work, smp, dsmp, c->d_status, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), smp, sizeof(float) * hs.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hd.data(), dsmp, sizeof(float) * hd.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "tangent pass");
+    std::vector<double> mbar((size_t)K, 0.0), wk;
+    double dm[3] = {0.0, 0.0, 0.0};
+    std::vector<double> dmb((size_t)K * 3, 0.0);
+    for (long long k = 0; k < K; ++k)
+        for (int r = 0; r < c->n_real; ++r) {
+            const size_t i = (size_t)r * (size_t)K + (size_t)k;
+            mbar[(size_t)k] += hs[i];
+            for (int j = 0; j < 3; ++j) dmb[(size_t)k * 3 + j] += hd[3 * i + j];
+        }
+    for (long long k = 0; k < K; ++k) {
+        mbar[(size_t)k] /= c->n_real;
+        for (int j = 0; j < 3; ++j) dmb[(size_t)k * 3 + j] /= c->n_real;
+    }
+    const double L = window_loss(d, c->sw, objective, target, k_first, K, mbar, wk);
+    for (long long k = 0; k < K; ++k)
+        for (int j = 0; j < 3; ++j) dm[j] += wk[(size_t)k] * dmb[(size_t)k * 3 + j];
+    for (int j = 0; j < 3; ++j) grad_out[j] = dm[j];
+    if (loss_out) *loss_out = L;
+    return LLG_OK;
+}
+
 llg_status llg_loop_area_grad(llg_ctx *c, int64_t n_steps, int objective, const double *target,
                               int64_t ckpt_every, double *loss_out, double grad_out[3])
 {
@@ -717,11 +811,6 @@ llg_status llg_loop_area_grad(llg_ctx *c, int64_t n_steps, int objective, const 
     kp.real0 = c->real0;
     s = ensure_axes(c, &kp.axis);
     if (s != LLG_OK) return s;
-    if (!llg::adjoint_supported(kp, c->device))
-        return fail(LLG_EUNSUPPORTED, "the adjoint handles rods of at most 1024 cells with free faces");
-    llg::RodPlan plan{};
-    if (!llg::rod_plan(kp, c->n_real, c->device, &plan, 1, 0, 0))
-        return fail(LLG_EUNSUPPORTED, "no resident forward plan for this grid");
     const long long step0 = c->step, N = n_steps, C = ckpt_every;
     const long long S = (N + C - 1) / C;
     const long long se = d.sample_every;
@@ -730,6 +819,13 @@ llg_status llg_loop_area_grad(llg_ctx *c, int64_t n_steps, int objective, const 
     if (K < 1) return fail(LLG_EINVAL, "the window holds no sample");
     if (k_last >= d.n_samples && d.n_half > 0) return fail(LLG_EINVAL, "the window runs past the end of the loop");
     const size_t state = (size_t)c->n_real * (size_t)ncells_of(c) * 3;
+    if (c->grad_method == 1) return tangent_grad(c, d, kp, n_steps, objective, target, k_first, K, state, loss_out,
+                                                 grad_out);
+    if (!llg::adjoint_supported(kp, c->device))
+        return fail(LLG_EUNSUPPORTED, "the adjoint handles rods of at most 1024 cells with free faces");
+    llg::RodPlan plan{};
+    if (!llg::rod_plan(kp, c->n_real, c->device, &plan, 1, 0, 0))
+        return fail(LLG_EUNSUPPORTED, "no resident forward plan for this grid");
     const long long ns_total = std::max<long long>(d.n_samples, k_last + 1);
     // store the whole window's states when they fit the budget and a quarter of the free memory
     bool store_all = false;
@@ -791,29 +887,13 @@ llg_status llg_loop_area_grad(llg_ctx *c, int64_t n_steps, int objective, const 
         return cuda_fail(e, "adjoint forward");
     }
     // loss and its weights on the realisation-mean samples
-    std::vector<double> mbar((size_t)K, 0.0), wk((size_t)K, 0.0), Hk((size_t)K);
+    std::vector<double> mbar((size_t)K, 0.0), wk;
     for (long long k = 0; k < K; ++k) {
         double sum = 0.0;
         for (int r = 0; r < c->n_real; ++r) sum += hs[(size_t)r * ns_total + (size_t)(k_first + k)];
         mbar[(size_t)k] = sum / c->n_real;
-        Hk[(size_t)k] = llg::field_Oe(d, c->sw, (k_first + k) * se);
     }
-    double L = 0.0;
-    if (objective == 0) {
-        for (long long k = 0; k < K; ++k) {
-            const double err = mbar[(size_t)k] - target[k_first + k];
-            L += err * err / (double)K;
-            wk[(size_t)k] = 2.0 * err / (double)K;
-        }
-    } else {
-        // signed trapezoid area of the window's mean loop, sum (m_k + m_k+1)/2 (H_k+1 - H_k)
-        for (long long k = 0; k + 1 < K; ++k) {
-            const double dH = Hk[(size_t)k + 1] - Hk[(size_t)k];
-            L += 0.5 * (mbar[(size_t)k] + mbar[(size_t)k + 1]) * dH;
-            wk[(size_t)k] += 0.5 * dH;
-            wk[(size_t)k + 1] += 0.5 * dH;
-        }
-    }
+    const double L = window_loss(d, c->sw, objective, target, k_first, K, mbar, wk);
     e = cudaMemcpyAsync(w, wk.data(), sizeof(double) * (size_t)K, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(lam, 0, sizeof(float) * state, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(partial, 0, sizeof(double) * 5 * (size_t)c->n_real, st);

@@ -144,6 +144,7 @@ extern "C" llg_status llg_autotune(llg_ctx *ctx, int64_t trial_steps, double *be
     for (int rows : {0, 1, 2, 3, 4}) cand.emplace_back(2, 0, rows, 0);
     for (int cpt : {0, 1, 2, 4})
         for (int rods : {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) cand.emplace_back(1, rods, 0, cpt);
+    for (int rods : {0, 1, 2, 4, 8, 16, 32}) cand.emplace_back(3, rods, 0, 0);
     const size_t bytes = (size_t)v.n_real * (size_t)v.kp.ncells * 3 * sizeof(float);
     float *scratch = nullptr;
     if (cudaMalloc(&scratch, bytes) != cudaSuccess) {

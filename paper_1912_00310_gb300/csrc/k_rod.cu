@@ -478,25 +478,33 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
-// Hand-off of the balanced schedule (McNaughton's wrap-around rule): all n_real * N rod-steps of
-// a launch laid end to end (rod r at positions [r N, (r + 1) N)) and cut into gridDim.x equal
-// slices of C = ceil(n_real N / gridDim.x) >= N positions.  A CTA walks its slice in order: a rod
-// cut at the slice's start is run for its FIRST steps (kind 1, then flags[rod] is released), whole
-// rods are run entirely (kind 0), and a rod cut at the slice's end is run for its LAST steps
-// (kind 2, after waiting for flags[rod]).  Because C >= N, the producer of a hand-off runs it at
-// the start of its own slice, long before the consumer reaches the end of its slice.  The schedule
-// is arithmetic on (n_real, N, gridDim.x), so each CTA derives its own segments.
+// Balanced schedule of one launch (McNaughton's wrap-around rule): all n_real * N rod-steps laid
+// end to end and cut into gridDim.x equal slices; a rod cut at a slice boundary runs its first
+// steps at the start of the next CTA's slice and its last steps at the end of this CTA's slice,
+// handed off through global memory.  Up to three segments per CTA {rod, first step offset,
+// steps, kind}: kind 0 whole rod, 1 first part (release flags[rod] when done), 2 last part (wait
+// for flags[rod] first).  Built on the host and passed as a kernel parameter, so the segment
+// fields are uniform constant-bank values: the rod index feeds the Philox round keys, which then
+// stay in uniform registers (measured on GB300: a schedule read from shared memory or walked
+// on the device cost 6-9 % of the b = 1 rate).
+constexpr int kMaxBalancedCtas = 256;
+struct BalancedSchedule {
+    int4 seg[3 * kMaxBalancedCtas];
+};
+
 struct HandoffCtl {
     unsigned long long timeout_ns;  // longest wait for a producer before giving up (status bit 1)
     int withhold;                   // test hook: producers do not release (every wait runs out)
 };
 
-// balanced == 0: one rod per CTA over [step0, step0 + n_steps).
-// balanced == 1: the wrap-around schedule above; needs all CTAs co-resident (cooperative launch).
+// balanced == 0: one rod per CTA over [step0, step0 + n_steps); balanced == 1: the segments of
+// `sched` (cooperative launch: all CTAs co-resident).  A wait for a hand-off gives up after
+// hc.timeout_ns: status bit 1 is set and the CTA skips its remaining segments.
 template <int R, int NX, int NY = 0, int NZ = 0, int SHAPE = -1, bool AX = false>
 __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_kernel(
-    KParams p, float *__restrict__ m_glob, long long step0, int n_steps, int n_real, float *__restrict__ samples,
-    int *__restrict__ status, unsigned *__restrict__ flags, int balanced, long long slice, HandoffCtl hc)
+    KParams p, float *__restrict__ m_glob, long long step0, int n_steps, float *__restrict__ samples,
+    int *__restrict__ status, unsigned *__restrict__ flags, int balanced,
+    const __grid_constant__ BalancedSchedule sched, HandoffCtl hc)
 {
     static_assert(NX >= 3 && NX % 2 == 0, "merged schedule with even plane count");
     extern __shared__ float4 sm4[];
@@ -504,41 +512,34 @@ __global__ void __launch_bounds__(pipelined_max_threads(R), 1) rod_pipelined_nx_
     for (int i = threadIdx.x; i < (NX + 2) * PL; i += blockDim.x) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     PipelinedRod<R, NX, NY, NZ, SHAPE, AX> w;
     w.setup(sm4, p);
-    // The segments of this CTA's slice, walked by every thread from uniform values only (the
-    // launch parameters and blockIdx), so the rod index -- and the Philox round keys run()
-    // derives from it -- stay warp-uniform; no 64-bit division (a called routine here): the
-    // host passes the slice length and the first rod is found by a walk over rods.  Without
-    // balancing the slice is rod blockIdx.x.  kind 1: the rod's first steps (then release
-    // flags[rod]); kind 2: its last steps (after waiting for flags[rod]; a wait that runs out
-    // sets status bit 1 and the CTA goes on, the result then being flagged); kind 0: all of it.
-    const long long N = n_steps, W = (long long)n_real * N;
-    const long long C = balanced ? slice : N;
-    const long long lo = min((long long)blockIdx.x * C, W), hi = min(lo + C, W);
-    int rod = balanced ? 0 : (int)blockIdx.x;
-    while ((long long)(rod + 1) * N <= lo) ++rod;
-    for (long long pos = lo; pos < hi; ++rod) {
-        const long long off = pos - (long long)rod * N;
-        const long long len = min(hi, (long long)(rod + 1) * N) - pos;
-        const int kind = off != 0 ? 1 : (len < N ? 2 : 0);
-        pos += len;
-        if (kind == 2) {
+    __syncthreads();
+    __shared__ int go;
+    const int nseg = balanced ? 3 : 1;
+    for (int i = 0; i < nseg; ++i) {
+        const int4 sg = balanced ? sched.seg[3 * blockIdx.x + i] : make_int4(blockIdx.x, 0, n_steps, 0);
+        if (sg.z <= 0) continue;
+        if (sg.w == 2) {
             if (threadIdx.x == 0) {
                 const unsigned long long t0 = globaltimer_ns();
-                while (ld_acquire_gpu(flags + rod) == 0u) {
+                int ok = 1;
+                while (ld_acquire_gpu(flags + sg.x) == 0u) {
                     if (globaltimer_ns() - t0 > hc.timeout_ns) {
+                        ok = 0;
                         atomicOr(status, 2);
                         break;
                     }
                     __nanosleep(200);
                 }
                 __threadfence();
+                go = ok;
             }
             __syncthreads();
+            if (!go) break;
         }
-        w.run(p, m_glob, rod, step0 + (kind == 2 ? N - len : 0), (int)len, samples, status);
-        if (kind == 1 && threadIdx.x == 0 && !hc.withhold) {
+        w.run(p, m_glob, sg.x, step0 + sg.y, sg.z, samples, status);
+        if (sg.w == 1 && threadIdx.x == 0 && !hc.withhold) {
             __threadfence();
-            st_release_gpu(flags + rod, 1u);
+            st_release_gpu(flags + sg.x, 1u);
         }
     }
 }
@@ -595,10 +596,40 @@ bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_ki
     const size_t pipe_bytes = ((size_t)p.nx + 2) * PL * sizeof(float4);
     const bool twophase_fits = rod_bytes <= (size_t)smem_optin && p.ncells <= 4 * kMaxThreads;
     const bool pipelined_fits = pipe_bytes <= (size_t)smem_optin && rows <= 4 * 672;
-    // Default (measured on GB300): rods of at most one CTA of threads use the two-phase kernel
-    // with one rod per CTA (many small CTAs per SM); larger rods use the plane-pipelined kernel.
+    // Default (measured on GB300): the b = 2, 4, 8 rods of the paper's ladder use the row kernel;
+    // other rods of at most one CTA of threads the two-phase kernel with one rod per CTA (many
+    // small CTAs per SM); larger rods the plane-pipelined kernel.
     int kind = force_kind;
-    if (kind == 0) kind = (p.ncells <= kMaxThreads && twophase_fits) ? 1 : (pipelined_fits ? 2 : 1);
+    if (kind == 0)
+        kind = rows_supported(p) ? 3 : ((p.ncells <= kMaxThreads && twophase_fits) ? 1 : (pipelined_fits ? 2 : 1));
+    if (kind == 3) {
+        if (!rows_supported(p)) return false;
+        const int maxt = rows_max_threads(p);
+        const size_t rbytes = rows_rod_bytes(p);
+        const int by_smem = (int)std::max<size_t>(1, (size_t)smem_optin / rbytes);
+        int rods = force_rods;
+        if (rods == 0) {
+            // one rod per CTA (measured on GB300 ahead of packing rods: 608 b = 4 rods at 9.9e10
+            // cell-steps/s), unless that leaves over a quarter of the last warp idle (the b = 8
+            // rod's 21 rows): then the fewest rods that leave at most a tenth of it
+            rods = 1;
+            if (4 * (round_warp(rows) - rows) > round_warp(rows))
+                for (int r = 2; r * rows <= maxt && r <= by_smem; ++r)
+                    if (10 * (round_warp(r * rows) - r * rows) <= round_warp(r * rows)) {
+                        rods = r;
+                        break;
+                    }
+        }
+        if (rods < 1 || rods > by_smem || round_warp(rods * rows) > maxt) return false;
+        plan->kind = 3;
+        plan->rods_per_cta = rods;
+        plan->cells_per_thread = p.nx;
+        plan->threads = round_warp(rods * rows);
+        plan->rows_per_thread = 1;
+        plan->smem_bytes = rods * rbytes;
+        plan->ctas = (n_real + rods - 1) / rods;
+        return true;
+    }
     if (kind == 1) {
         if (!twophase_fits || p.sample_every >= (1LL << 31)) return false;
         // cells per thread: forced, or the fewest that hold one rod in one CTA
@@ -647,6 +678,41 @@ static cudaError_t set_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// McNaughton's wrap-around schedule of n_real rods x N steps over G co-resident CTAs; false when
+// some CTA's slice would need more than three segments (more than about two waves of rods),
+// in which case the launch is not balanced.
+static bool balanced_schedule(int n_real, int N, int G, BalancedSchedule *sc)
+{
+    if (G > kMaxBalancedCtas) return false;
+    std::memset(sc, 0, sizeof *sc);
+    const long long W = (long long)n_real * N;
+    const long long C = (W + G - 1) / G;
+    for (int j = 0; j < G; ++j) {
+        const long long lo = std::min((long long)j * C, W), hi = std::min(lo + C, W);
+        int k = 0;
+        for (long long pos = lo; pos < hi;) {
+            if (k == 3) return false;
+            const long long rod = pos / N, off = pos - rod * N;
+            const long long len = std::min(hi, (rod + 1) * N) - pos;
+            int4 &g = sc->seg[3 * j + k++];
+            g.x = (int)rod;
+            g.z = (int)len;
+            if (off != 0) {  // first len steps, then hand off
+                g.y = 0;
+                g.w = 1;
+            } else if (len < N) {  // last len steps, after the hand-off
+                g.y = (int)(N - len);
+                g.w = 2;
+            } else {
+                g.y = 0;
+                g.w = 0;
+            }
+            pos += len;
+        }
+    }
+    return true;
+}
+
 // Launch of the nx-specialised kernel: balanced over a co-resident grid when the rods do not
 // divide evenly into waves, else one rod per CTA.
 template <int R, int NX, int NY = 0, int NZ = 0, bool AX = false>
@@ -663,19 +729,19 @@ static cudaError_t launch_nx(const KParams &p, const RodPlan &plan, float *m, in
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, plan.threads, plan.smem_bytes)) != cudaSuccess)
         return e;
     const int resident = nsm * per_sm;
-    int ns = (int)n_steps;  // rod_advance splits longer runs
+    BalancedSchedule sched;
+    int ns = (int)n_steps;
     HandoffCtl hc{plan.handoff_timeout_ns, plan.withhold_handoff ? 1 : 0};
-    // balance when the rods do not fill whole waves
-    if (plan.balance && flags && resident > 0 && n_real > resident && n_real % resident != 0) {
+    if (plan.balance && flags && resident > 0 && n_real > resident && n_real % resident != 0 &&
+        balanced_schedule(n_real, ns, resident, &sched)) {
         if ((e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)n_real, st)) != cudaSuccess) return e;
         int balanced = 1;
-        long long slice = ((long long)n_real * ns + resident - 1) / resident;  // rod-steps per CTA
-        void *args[] = {(void *)&p, (void *)&m, (void *)&step0, (void *)&ns, (void *)&n_real, (void *)&samples,
-                        (void *)&status, (void *)&flags, (void *)&balanced, (void *)&slice, (void *)&hc};
+        void *args[] = {(void *)&p, (void *)&m, (void *)&step0, (void *)&ns, (void *)&samples,
+                        (void *)&status, (void *)&flags, (void *)&balanced, (void *)&sched, (void *)&hc};
         return cudaLaunchCooperativeKernel((const void *)kern, dim3(resident), dim3(plan.threads), args,
                                            plan.smem_bytes, st);
     }
-    kern<<<n_real, plan.threads, plan.smem_bytes, st>>>(p, m, step0, ns, n_real, samples, status, flags, 0, 0LL, hc);
+    kern<<<n_real, plan.threads, plan.smem_bytes, st>>>(p, m, step0, ns, samples, status, flags, 0, sched, hc);
     return cudaGetLastError();
 }
 
@@ -699,6 +765,9 @@ cudaError_t rod_advance(const KParams &p, const RodPlan &plan, float *m, int n_r
     cudaError_t e = cudaSuccess;
     if (plan.kind == 1) {
         e = twophase_advance(p, plan, m, n_real, step0, (int)n_steps, samples, status, st);
+        if (e != cudaSuccess) return e;
+    } else if (plan.kind == 3) {
+        e = rows_advance(p, plan, m, n_real, step0, (int)n_steps, samples, status, st);
         if (e != cudaSuccess) return e;
     } else if (plan.kind == 2 && p.axis && plan.rows_per_thread == 3 && p.nx == 8 && p.ny == 24 && p.nz == 56 &&
                !plan.generic) {

@@ -104,7 +104,8 @@ cudaError_t axis_fill(float4 *ax, int n_real, int ncells, uint32_t seed, uint32_
 
 // ---- resident engine (k_rod.cu): rods in shared memory for the whole launch ------------------
 struct RodPlan {
-    int kind;          // 1: two-phase (small rods, several per CTA); 2: plane-pipelined (one per CTA)
+    int kind;          // 1: two-phase (small rods, several per CTA); 2: plane-pipelined (one per CTA);
+                       // 3: rows (the b = 2, 4, 8 rods, a thread per x-row, several rods per CTA)
     int rods_per_cta;  // kind 1
     int threads;
     int rows_per_thread;  // kind 2
@@ -124,6 +125,13 @@ bool rod_plan(const KParams &p, int n_real, int dev, RodPlan *plan, int force_ki
 // Two-phase kernel (k_rod_small.cu): whether the grid and sweep have a compile-time instance,
 // the largest CTA for cpt cells per thread, and the launch of n_steps (< 2^31) steps.
 bool twophase_shaped(const KParams &p);
+// Row kernel (k_rod_small.cu, plan kind 3): the b = 2, 4, 8 rods with a compile-time instance,
+// its largest CTA, the shared memory of one rod, and the launch.
+bool rows_supported(const KParams &p);
+int rows_max_threads(const KParams &p);
+size_t rows_rod_bytes(const KParams &p);
+cudaError_t rows_advance(const KParams &p, const RodPlan &plan, float *m, int n_real, long long step0, int n_steps,
+                         float *samples, int *status, cudaStream_t st);
 int twophase_max_threads(const KParams &p, int cpt);
 cudaError_t twophase_advance(const KParams &p, const RodPlan &plan, float *m, int n_real, long long step0,
                              int n_steps, float *samples, int *status, cudaStream_t st);
@@ -164,6 +172,15 @@ cudaError_t adjoint_recompute_all(const KParams &p, int n_real, long long step0,
 cudaError_t adjoint_backward_all(const KParams &p, int n_real, long long step0, long long n_steps, long long k_first,
                                  int n_k, const float *states, float *lam, const double *w, double *partial,
                                  cudaStream_t st);
+
+// ---- tangent gradient (k_tangent.cu): one pass, one CTA per rod, rods of at most 1024 cells -----
+bool tangent_supported(const KParams &p, int dev);
+// dcoef: the derivatives of (c_ex, c_an, alpha, a = dt g1) and dsigma/sigma with respect to
+// (s_K, s_alpha, s_Ms), five groups of three.  m_work (advanced in place), samples [n_real][n_k]
+// and dsamples [n_real][n_k][3] for the samples k_first .. k_first + n_k - 1 of the window.
+cudaError_t tangent_forward(const KParams &p, const double dcoef[15], int n_real, long long step0, long long n_steps,
+                            long long k_first, int n_k, float *m_work, float *samples, float *dsamples, int *status,
+                            cudaStream_t st);
 
 // ---- host runtime helpers (api.cpp) ---------------------------------------------------------
 // Store a message for llg_last_error() on this thread.

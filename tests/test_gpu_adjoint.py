@@ -178,4 +178,36 @@ def test_stored_window_equals_segment_by_segment(pkg, ckpt_every, disp):
         assert g.step == 150
         g.close()
     assert out[0][0] == out[1][0]
-    assert np.allclose(out[0][1], out[1][1], rtol=1e-5, atol=0)
+    # measured on the calibration workload: the two schedules agree bitwise with aligned segments,
+    # and regrouping the FP32 block sums moves the gradient by at most 2e-8 relative (against a
+    # per-step FP64 accumulation)
+    assert np.allclose(out[0][1], out[1][1], rtol=1e-7, atol=0)
+
+
+@pytest.mark.parametrize("disp,shape", [(0.0, 0), (0.3, 1)])
+def test_tangent_method_matches_adjoint_and_oracle(pkg, orc, disp, shape):
+    """The forward-mode method (LLG_TUNE_GRAD_METHOD 1): the same loss as the adjoint, bitwise (its
+    primal is the forward run's arithmetic), and a gradient within 1e-2 of the FP64 forward-mode
+    oracle gradient with no absolute floor and within 1e-4 of the reverse-mode adjoint (the two
+    FP32 methods differ only in rounding); with dispersed axes under the sinusoid too."""
+    dims, n_real, n_steps = ROD_DIMS[4], 8, 3000
+    g = grid(pkg, dims)
+    if shape == 1:
+        g.set_sweep(H_start=1500.0, H_turn=0.0, rate=1000.0, dt=10e-15, sample_dH=1.0, shape=1)
+    g.set_axis_dispersion(disp)
+    target = target_for(g)
+    out = {}
+    for method in (0, 1):
+        g.set_tuning(pkg.TUNE_GRAD_METHOD, method)
+        g.reset(seed=4, n_real=n_real)
+        out[method] = g.loss_grad(n_steps, target, 0, 256)
+        assert g.step == 0
+    assert out[0][0] == out[1][0]
+    assert np.allclose(out[1][1], out[0][1], rtol=1e-4, atol=0), (out[0][1], out[1][1])
+    if shape == 0 and disp == 0.0:
+        m0 = orc.uniform_state(n_real, g.ncells)
+        Lo, go, _ = oracle_grad(orc, dims, m0, (1.0, 1.0, 1.0), 0, n_steps, target, seed=4)
+        assert out[1][0] == pytest.approx(Lo, rel=1e-3)
+        for k in range(3):
+            assert out[1][1][k] == pytest.approx(go[k], rel=1e-2), (k, out[1][1], go)
+    g.close()

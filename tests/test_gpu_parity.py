@@ -111,13 +111,19 @@ def test_trajectory_parity_first_1000_steps(pkg, orc, dims, b, engine, kind, n_r
     g.close()
 
 
-@pytest.mark.parametrize("dims,b,n_real", [(ROD_DIMS[4], 4, 6), (ROD_DIMS[2], 2, 3), (ROD_DIMS[1], 1, 2)])
+@pytest.mark.parametrize("dims,b,n_real", [(ROD_DIMS[4], 4, 6), (ROD_DIMS[2], 2, 3), (ROD_DIMS[1], 1, 2),
+                                            (ROD_DIMS[8], 8, 37)])
 def test_engines_bitwise_equal(pkg, dims, b, n_real):
+    """Plain engine, two-phase, plane-pipelined and (b = 2, 4, 8) row kernels: bitwise-equal states
+    and samples; 37 b = 8 rods leave a partial last CTA of the row kernel (32 rods per CTA)."""
     dt = DT_BY_B[b]
     outs = []
-    for eng, kind in ((pkg.ENGINE_PLAIN, 0), (pkg.ENGINE_RESIDENT, 1), (pkg.ENGINE_RESIDENT, 2)):
+    for eng, kind in ((pkg.ENGINE_PLAIN, 0), (pkg.ENGINE_RESIDENT, 1), (pkg.ENGINE_RESIDENT, 2),
+                      (pkg.ENGINE_RESIDENT, 3)):
         if kind == 1 and b == 1:
             continue  # the b = 1 rod does not fit the two-phase kernel
+        if kind == 3 and b == 1:
+            continue  # the row kernel serves the b = 2, 4, 8 rods
         g = make_grid(pkg, dims, b, dt, engine=eng, kind=kind)
         g.reset(seed=3, n_real=n_real, real_offset=11)
         S = torch.full((n_real, g.n_samples), float("nan"), device="cuda")

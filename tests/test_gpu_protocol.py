@@ -355,17 +355,23 @@ def test_protocol_runner_matches_oracle_statistics(pkg, orc):
     assert r["slp_W_per_g_at_alpha_0p1"] > 0
 
 
-@pytest.mark.parametrize("dims,rods,disp", [((10, 10, 10), 1, 0.3), ((12, 12, 12), 1, 0.3),
-                                            ((12, 12, 12), 1, 0.0), (ROD_DIMS[4], 3, 0.3)])
-def test_twophase_variants_bitwise_with_plain(pkg, dims, rods, disp):
-    """The two-phase kernel with two and four cells per thread (1000- and 1728-cell grids) and with
-    three rods per CTA, under the sinusoid, with and without dispersed axes: bitwise equal to the
+@pytest.mark.parametrize("dims,rods,disp,kind,cpt", [((10, 10, 10), 1, 0.3, 1, 0), ((12, 12, 12), 1, 0.3, 1, 0),
+                                                     ((12, 12, 12), 1, 0.0, 1, 0), (ROD_DIMS[4], 3, 0.3, 1, 0),
+                                                     (ROD_DIMS[4], 2, 0.3, 1, 2), (ROD_DIMS[4], 1, 0.0, 1, 4),
+                                                     (ROD_DIMS[4], 3, 0.3, 3, 0), (ROD_DIMS[2], 1, 0.3, 3, 0),
+                                                     (ROD_DIMS[8], 5, 0.3, 3, 0)])
+def test_twophase_variants_bitwise_with_plain(pkg, dims, rods, disp, kind, cpt):
+    """The two-phase kernel with two and four cells per thread (1000- and 1728-cell grids, and the
+    b = 4 rod's compile-time instances), with several rods per CTA, and the row kernel of the
+    b = 2, 4, 8 rods, under the sinusoid, with and without dispersed axes: bitwise equal to the
     plain engine."""
     n_real, outs = 5, []
-    for eng, kind in ((pkg.ENGINE_RESIDENT, 1), (pkg.ENGINE_PLAIN, 0)):
-        g = sine_grid(pkg, dims, 4, engine=eng, kind=kind)
-        if rods > 1:
+    for eng, kd in ((pkg.ENGINE_RESIDENT, kind), (pkg.ENGINE_PLAIN, 0)):
+        g = sine_grid(pkg, dims, 4, engine=eng, kind=kd)
+        if rods > 1 and kd:
             g.set_tuning(pkg.TUNE_RODS_PER_CTA, rods)
+        if cpt and kd:
+            g.set_tuning(pkg.TUNE_CELLS_PER_THREAD, cpt)
         g.set_axis_dispersion(disp)
         g.reset(seed=12, n_real=n_real)
         g.advance(60)
