@@ -54,7 +54,7 @@ def parse():
                          "10 Oe/ns); not part of the default benchmark")
     ap.add_argument("--profile-case", default=None,
                     help="run a small untimed case for a profiler (b1, b1-plain, b4, b4-rows, slab, "
-                         "adjoint) and exit")
+                         "adjoint, tangent) and exit")
     return ap.parse_args()
 
 
@@ -712,18 +712,20 @@ def profile_case(name):
         # the 512x512x56 periodic slab (14.7M cells, 470 MB of state buffers), a few Heun steps
         cfg = dict(CONFIGS["slab_512x512x56"], sample_dH=1.0)
         n_real, steps, eng = 1, 4, pkg.ENGINE_STREAM
-    elif name == "adjoint":
-        # the calibration workload's rod and ensemble on a 2000-step window (stored window: one
-        # recompute launch and one reverse launch per gradient), two gradients
+    elif name in ("adjoint", "tangent"):
+        # the calibration workload's rod and ensemble on a 2000-step window, two gradients: the
+        # adjoint (stored window: one recompute launch and one reverse launch per gradient) or
+        # the tangent method (one launch per gradient)
         import numpy as np
         c5 = CONFIGS["adjoint_b4"]
         g = make_grid(pkg, dict(c5, sample_dH=1.0), pkg.ENGINE_RESIDENT)
+        g.set_tuning(pkg.TUNE_GRAD_METHOD, 1 if name == "tangent" else 0)
         g.reset(seed=0, n_real=c5["n_real"])
         target = 0.9 + 0.05 * np.cos(np.arange(g.n_samples) / 7.0)
         for _ in range(2):
             g.loss_grad(2000, target, 0, c5["ckpt_every"])
         g.close()
-        print("profile case adjoint: 64 rods x 2000-step window x 2 gradients done")
+        print(f"profile case {name}: 64 rods x 2000-step window x 2 gradients done")
         return 0
     else:
         raise SystemExit(f"unknown profile case {name}")

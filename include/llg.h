@@ -300,7 +300,8 @@ llg_status llg_autotune(llg_ctx *ctx, int64_t trial_steps, double *best_rate);
  * recomputes the segment's states from its checkpoint and runs the reverse-mode adjoint of the
  * Heun step back through them (one CTA per realisation; rods of at most 1024 cells with free
  * faces).  Method 1: one forward pass carrying the tangents dm/d(s_K, s_alpha, s_Ms) beside the
- * state (ckpt_every unused).  Either allocates its scratch for the duration of the call and
+ * state (one CTA per realisation and parameter; rods of at most 1408 cells with free faces, the
+ * b = 2 rod included; ckpt_every unused).  Either allocates its scratch for the duration of the call and
  * synchronises.
  * loss_out (optional) receives L; grad_out receives dL/d(s_K, s_alpha, s_Ms).
  * Errors: EINVAL (no ensemble, no sample in the window, window past the loop end),

@@ -739,7 +739,7 @@ static llg_status tangent_grad(llg_ctx *c, const llg::Derived &d, const llg::KPa
                                double grad_out[3])
 {
     if (!llg::tangent_supported(kp, c->device))
-        return fail(LLG_EUNSUPPORTED, "the tangent method handles rods of at most 256 cells with free faces");
+        return fail(LLG_EUNSUPPORTED, "the tangent method handles rods of at most 1408 cells with free faces");
     if (K > 0x7fffffffLL) return fail(LLG_EINVAL, "too many samples in the window");
     const double sK = c->sc.sK, sA = c->sc.sAlpha, sM = c->sc.sMs;
     const double alpha = d.alpha, a = c->sw.dt * d.g1;

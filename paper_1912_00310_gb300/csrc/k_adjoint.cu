@@ -20,7 +20,8 @@
 // and dL/dm of the previous state is g_m.  The host maps (g_alpha, g_a, g_cex, g_can, g_sigma)
 // to the scale factors (g_sigma is accumulated as g_H.h_th, i.e. sigma dL/dsigma).
 //
-// One CTA per rod, one cell per thread, the rod in shared memory with a zero ghost layer.  The
+// One CTA per rod, one cell per thread, the rod in shared memory (compact, with one zero slot for
+// the neighbours beyond a free face).  The
 // kernel has two phases: recompute the states of a checkpoint segment forward from its checkpoint
 // (bitwise the forward run: same arithmetic) into global memory, and walk stored states backward.
 // With memory to spare (the whole window's states, 12 bytes per cell, realisation and step), one
@@ -33,6 +34,7 @@
 
 #include "llg_internal.h"
 #include "physics.cuh"
+#include "sweep32.cuh"
 
 namespace llg {
 namespace {
@@ -62,40 +64,58 @@ struct AdjParams {
     long long n_total;    // ... and the window has n_total steps (the last segment is shorter)
 };
 
-// Neighbour sum over the six faces (x-, x+, y-, y+, z-, z+) of a ghost-padded rod.
-__device__ __forceinline__ float3 nsum(const float4 *A, int q, int sy, int sz)
+// The rod in shared memory is compact: one float4 per cell in cell order plus one zero slot that
+// stands for every neighbour beyond a free face, so that consecutive threads read consecutive
+// float4s (a ghost-padded layout of a thin rod leaves most banks of each row unused and every
+// neighbour load conflicted).  Neighbour indices of a cell in the order x-, x+, y-, y+, z-, z+.
+struct Nbr {
+    int i[6];
+};
+
+__device__ __forceinline__ Nbr neighbours(int c, int nx, int ny, int nz, int zero)
 {
-    float3 nb = add3(xyz(A[q - 1]), xyz(A[q + 1]));
-    nb = add3(nb, xyz(A[q - sy]));
-    nb = add3(nb, xyz(A[q + sy]));
-    nb = add3(nb, xyz(A[q - sz]));
-    return add3(nb, xyz(A[q + sz]));
+    const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny), sxy = nx * ny;
+    Nbr n;
+    n.i[0] = x > 0 ? c - 1 : zero;
+    n.i[1] = x < nx - 1 ? c + 1 : zero;
+    n.i[2] = y > 0 ? c - nx : zero;
+    n.i[3] = y < ny - 1 ? c + nx : zero;
+    n.i[4] = z > 0 ? c - sxy : zero;
+    n.i[5] = z < nz - 1 ? c + sxy : zero;
+    return n;
+}
+
+// Neighbour sum over the six faces (x-, x+, y-, y+, z-, z+), every engine's order.
+__device__ __forceinline__ float3 nsum(const float4 *A, const Nbr &n)
+{
+    float3 nb = add3(xyz(A[n.i[0]]), xyz(A[n.i[1]]));
+    nb = add3(nb, xyz(A[n.i[2]]));
+    nb = add3(nb, xyz(A[n.i[3]]));
+    nb = add3(nb, xyz(A[n.i[4]]));
+    return add3(nb, xyz(A[n.i[5]]));
 }
 
 // MAXT: the largest CTA the instance runs with (256 for rods up to 256 cells, which then get up to
-// 255 registers per thread, 1024 otherwise).
-template <bool AX, int MAXT>
+// 255 registers per thread, 1024 otherwise); SHAPE: the sweep shape with 32-bit bookkeeping (0
+// triangle, 1 cosine) or -1 for the 64-bit sweep of any period.
+template <bool AX, int MAXT, int SHAPE>
 __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
     AdjParams ap, const float *__restrict__ ckpt, float *__restrict__ seg, float *__restrict__ lam,
     const double *__restrict__ w, double *__restrict__ partial)
 {
     extern __shared__ float4 sm4[];
     const KParams &p = ap.p;
-    const int px = p.nx + 2, py = p.ny + 2;
-    const int sy = px, sz = px * py;
-    const int rod_pad = sz * (p.nz + 2);
-    float4 *M = sm4, *P = M + rod_pad, *GT = P + rod_pad, *GH = GT + rod_pad;
-    const int rod = blockIdx.x;
     const int ncell = p.ncells;
+    const int S = ncell + 1;  // cells and the zero slot
+    float4 *M = sm4, *P = M + S, *GT = P + S, *GH = GT + S;
+    const int rod = blockIdx.x;
     const int c = threadIdx.x;
     const bool act = c < ncell;
-    for (int i = threadIdx.x; i < 4 * rod_pad; i += blockDim.x) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    int q = 0;
-    if (act) {
-        const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
-        q = (x + 1) + sy * (y + 1) + sz * (z + 1);
-    }
+    for (int i = threadIdx.x; i < 4 * S; i += blockDim.x) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const Nbr nb = neighbours(act ? c : 0, p.nx, p.ny, p.nz, ncell);
+    const int q = c;  // this cell's slot
     const uint32_t real = p.real0 + (uint32_t)rod;
+    const PhiloxKeys keys = philox_keys(p.seed, real);  // the rod's round keys, formed once
     const size_t state = (size_t)ncell * 3;
     const size_t rod_off = (size_t)rod * state;
     const int n_rods = gridDim.x;
@@ -119,7 +139,7 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
     __syncthreads();
 
     // ---- forward recomputation of the segment: seg[j] = state before step seg_start + j ----
-    Sweep field;
+    typename SweepSel<SHAPE>::type field;
     field.init(seg_start, p);
     float Hn = field.value();
     for (int j = 0; j < ((ap.phases & 1) ? seg_len : 0); ++j) {
@@ -136,8 +156,8 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
         }
         __syncthreads();
         if (act) {
-            h = thermal_field(p.seed, real, (uint32_t)c, n, p.sigma);
-            const float3 H = field_of(nsum(M, q, sy, sz), m, h, Hn);
+            h = thermal_field(keys, (uint32_t)c, n, p.sigma);
+            const float3 H = field_of(nsum(M, nb), m, h, Hn);
             const float3 s0 = llg_torque(m, H, p.alpha);
             P[q] = pad4(normalised(axpy(p.neg_dt_g1, s0, m)));
             acc = axpy(p.neg_hdt_g1, s0, m);
@@ -145,7 +165,7 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
         __syncthreads();
         if (act) {
             const float3 t = xyz(P[q]);
-            const float3 H = field_of(nsum(P, q, sy, sz), t, h, Hn1);
+            const float3 H = field_of(nsum(P, nb), t, h, Hn1);
             m = normalised(axpy(p.neg_hdt_g1, llg_torque(t, H, p.alpha), acc));
         }
         __syncthreads();
@@ -174,6 +194,12 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
     const float ha = -p.neg_hdt_g1;
     const float alpha = p.alpha;
     field.init(seg_start + seg_len - 1, p);
+    // sample bookkeeping of the reverse walk in 32 bits: done = n + 1 runs down from
+    // seg_start + seg_len; r = done mod sample_every, kd = done / sample_every (the host keeps
+    // sample_every below 2^31)
+    const long long se = p.sample_every;
+    int r_s = se > 0 ? (int)((seg_start + seg_len) % se) : -1;
+    long long kd = se > 0 ? (seg_start + seg_len) / se : 0;
     // Three barriers per reversed step.  The state before step j sits in M from the previous
     // iteration (it is stored there with the last shared write of that iteration, after every
     // read of M), and the stored state of the next step to reverse is loaded one step ahead (a
@@ -188,17 +214,22 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
     for (int j = seg_len - 1; j >= 0; --j) {
         const long long n = seg_start + j;
         const float hn = field.value();
-        Sweep f1 = field;
+        auto f1 = field;
         f1.inc();
         const float hn1 = f1.value();
         // loss gradient of the state after step n, if it is a sample of the window
-        const long long done = n + 1;
-        if (p.sample_every > 0 && done % p.sample_every == 0 && done <= ap.win_end) {
-            const long long k = done / p.sample_every - ap.k_first;
+        if (r_s == 0 && n + 1 <= ap.win_end) {
+            const long long k = kd - ap.k_first;
             if (k >= 0 && k < ap.n_k) g.z += (float)w[k] * ap.inj_scale;
         }
+        if (r_s == 0) {
+            r_s = (int)se - 1;
+            --kd;
+        } else if (r_s > 0) {
+            --r_s;
+        }
         float3 mi = zero3a(), h = zero3a(), H = zero3a(), c0 = zero3a(), s0 = zero3a(), t = zero3a();
-        float pn = 1.f;
+        float pn = 1.f;  // 1 / |p|
         if (act) {
             mi = m_cur;
             if (j > 0) {
@@ -208,13 +239,13 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
         }
         float3 Nm = zero3a();
         if (act) {
-            h = thermal_field(p.seed, real, (uint32_t)c, (unsigned long long)n, p.sigma);
-            Nm = nsum(M, q, sy, sz);
+            h = thermal_field(keys, (uint32_t)c, (unsigned long long)n, p.sigma);
+            Nm = nsum(M, nb);
             H = field_of(Nm, mi, h, hn);
             c0 = cross3(mi, H);
             s0 = llg_torque(mi, H, alpha);
             const float3 pv = axpy(p.neg_dt_g1, s0, mi);
-            pn = sqrtf(dot3(pv, pv));
+            pn = rsqrtf(dot3(pv, pv));  // 1 / |p|
             t = normalised(pv);
             P[q] = pad4(t);
         }
@@ -222,14 +253,14 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
         float3 gHt = zero3a(), Nt = zero3a(), c1 = zero3a(), gq = zero3a(), gmt = zero3a(), Ht = zero3a();
         float3 s1 = zero3a();
         if (act) {
-            Nt = nsum(P, q, sy, sz);
+            Nt = nsum(P, nb);
             Ht = field_of(Nt, t, h, hn1);
             c1 = cross3(t, Ht);
             s1 = llg_torque(t, Ht, alpha);
             const float3 qv = axpy(p.neg_hdt_g1, add3(s0, s1), mi);
-            const float qn = sqrtf(dot3(qv, qv));
-            const float3 mp = scale3(1.f / qn, qv);
-            gq = scale3(1.f / qn, sub3(g, scale3(dot3(mp, g), mp)));
+            const float rq = rsqrtf(dot3(qv, qv));  // 1 / |q|: m' = rq q, the forward's normalisation
+            const float3 mp = scale3(rq, qv);
+            gq = scale3(rq, sub3(g, scale3(dot3(mp, g), mp)));
             const float3 gs1 = scale3(-ha, gq);
             f_a -= 0.5f * dot3(add3(s0, s1), gq);
             const float3 gc1 = add3(gs1, scale3(alpha, cross3(gs1, t)));
@@ -241,7 +272,7 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
         __syncthreads();
         float3 gH = zero3a(), gm = zero3a();
         if (act) {
-            gmt = axpy(p.c_ex, nsum(GT, q, sy, sz), gmt);
+            gmt = axpy(p.c_ex, nsum(GT, nb), gmt);
             if constexpr (AX) {
                 const float gu = dot3(gHt, u);
                 gmt = axpy(p.c_an * gu, u, gmt);
@@ -252,7 +283,7 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
             }
             f_cex += dot3(gHt, Nt);
             f_sigma += dot3(gHt, h);  // d/dsigma = (1/sigma) g_H.h, divided on the host
-            const float3 gp = scale3(1.f / pn, sub3(gmt, scale3(dot3(t, gmt), t)));
+            const float3 gp = scale3(pn, sub3(gmt, scale3(dot3(t, gmt), t)));
             gm = add3(gq, gp);                                     // q = m - ..., p = m - a s0
             const float3 gs0 = add3(scale3(-ha, gq), scale3(-a, gp));  // from q and from p
             f_a -= dot3(s0, gp);
@@ -265,7 +296,7 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
         }
         __syncthreads();
         if (act) {
-            gm = axpy(p.c_ex, nsum(GH, q, sy, sz), gm);
+            gm = axpy(p.c_ex, nsum(GH, nb), gm);
             if constexpr (AX) {
                 const float gu = dot3(gH, u);
                 gm = axpy(p.c_an * gu, u, gm);
@@ -315,8 +346,7 @@ bool adjoint_supported(const KParams &p, int dev)
 {
     int smem_optin = 0;
     if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
-    const size_t rod_pad = (size_t)(p.nx + 2) * (p.ny + 2) * (p.nz + 2);
-    return p.periodic == 0 && p.ncells <= 1024 && 4 * rod_pad * sizeof(float4) <= (size_t)smem_optin;
+    return p.periodic == 0 && p.ncells <= 1024 && 4 * (size_t)(p.ncells + 1) * sizeof(float4) <= (size_t)smem_optin;
 }
 
 namespace {
@@ -324,19 +354,24 @@ cudaError_t launch_adjoint(const AdjParams &ap, int n_real, int n_seg, const flo
                            const double *w, double *partial, cudaStream_t st)
 {
     const KParams &p = ap.p;
-    const size_t rod_pad = (size_t)(p.nx + 2) * (p.ny + 2) * (p.nz + 2);
-    const size_t smem = 4 * rod_pad * sizeof(float4);
+    const size_t smem = 4 * (size_t)(p.ncells + 1) * sizeof(float4);
     const int threads = (p.ncells + 31) / 32 * 32;
     const dim3 grid((unsigned)n_real, (unsigned)n_seg);
+    if (p.sample_every >= (1LL << 31)) return cudaErrorInvalidValue;
+    // the sweep shape at compile time where its period fits 32 bits
+    const int shape = sweep_fits_32(p) ? (p.shape == 1 ? 1 : 0) : -1;
     auto go = [&](auto kern) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<grid, threads, smem, st>>>(ap, ckpt, seg, lam, w, partial);
         return cudaGetLastError();
     };
-    if (threads <= 256)
-        return p.axis ? go(adjoint_segment_kernel<true, 256>) : go(adjoint_segment_kernel<false, 256>);
-    return p.axis ? go(adjoint_segment_kernel<true, 1024>) : go(adjoint_segment_kernel<false, 1024>);
+    auto by_shape = [&](auto k0, auto k1, auto kg) { return shape == 0 ? go(k0) : shape == 1 ? go(k1) : go(kg); };
+#define LLG_ADJ(AXV, T) \
+    adjoint_segment_kernel<AXV, T, 0>, adjoint_segment_kernel<AXV, T, 1>, adjoint_segment_kernel<AXV, T, -1>
+    if (threads <= 256) return p.axis ? by_shape(LLG_ADJ(true, 256)) : by_shape(LLG_ADJ(false, 256));
+    return p.axis ? by_shape(LLG_ADJ(true, 1024)) : by_shape(LLG_ADJ(false, 1024));
+#undef LLG_ADJ
 }
 
 AdjParams adj_params(const KParams &p, int n_real, long long seg_start, int seg_len, long long win_end,

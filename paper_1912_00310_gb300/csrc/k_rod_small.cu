@@ -20,6 +20,7 @@
 #include "llg_internal.h"
 #include "physics.cuh"
 #include "reduce.cuh"
+#include "sweep32.cuh"
 
 namespace llg {
 namespace {
@@ -27,49 +28,6 @@ namespace {
 constexpr int kMaxThreads = 768;
 
 __device__ __forceinline__ float3 zero3t() { return make_float3(0.f, 0.f, 0.f); }
-
-// The Zeeman field of physics.cuh's SweepOf with the phase in 32 bits (the host uses this only for
-// periods below 2^31 steps); SHAPE 0 triangle, 1 cosine.  Same values as SweepOf: the triangle
-// coordinate min(ph, period - ph) and the cosine argument convert the same integers to float.
-template <int SHAPE>
-struct Sweep32 {
-    int ph, period;
-    float a, c;
-    __device__ __forceinline__ void init(long long n, const KParams &p)
-    {
-        long long per;
-        if constexpr (SHAPE == 0) {
-            per = 2 * p.n_half;
-            a = p.H0;
-        } else {
-            per = p.period;
-            a = p.amp;
-        }
-        c = p.slope;
-        period = (int)per;
-        ph = per > 0 ? (int)(n % per) : 0;
-    }
-    __device__ __forceinline__ float value() const
-    {
-        if constexpr (SHAPE == 1) return a * cospif(2.0f * ((float)ph / (float)period));
-        const int tri = min(ph, period - ph);
-        return fmaf(c, (float)tri, a);
-    }
-    __device__ __forceinline__ void inc()
-    {
-        if (period > 0 && ++ph == period) ph = 0;
-    }
-};
-
-// The 64-bit sweep for the runtime-shape instance (any period).
-template <int SHAPE>
-struct SweepSel {
-    using type = Sweep32<SHAPE>;
-};
-template <>
-struct SweepSel<-1> {
-    using type = Sweep;
-};
 
 // Rod extents: NXC > 0 at compile time, else from the kernel parameters.
 template <int NXC, int NYC, int NZC>

@@ -17,14 +17,20 @@
 // of a forward run.  At each sample of the window the kernel writes the cell average of m_z and of
 // the three dm_z/dtheta_j; the host forms dL/dtheta_j = sum_k (dL/dmbar_k) dmbar_k/dtheta_j.
 //
-// One CTA per rod, three threads per cell (one per tangent), the rod in shared memory with a zero
-// ghost layer: the state m and the three tangents in four float4 arrays, the same for the
-// predictor (64 bytes a cell and buffer); rods of at most 256 cells.
+// One CTA per rod and parameter (grid n_real x 3): CTA (r, j) recomputes rod r's primal, with the
+// forward engines' arithmetic (every CTA of a rod holds bitwise the same m), and carries the tangent
+// dm/dtheta_j; one or two cells per thread.  The rod sits in shared memory compactly, one float4
+// per cell in cell order plus one zero slot that stands for every neighbour beyond a free face (each
+// thread keeps its six neighbour indices): consecutive threads read consecutive float4s, without
+// the bank conflicts of a ghost-padded layout whose rows are only partly used.  Four such arrays:
+// m and dm/dtheta_j for the state and for the predictor (64 bytes a cell); rods of at most 1408
+// cells, the b = 2 rod included.
 #include <cmath>
 
 #include "llg_internal.h"
 #include "physics.cuh"
 #include "reduce.cuh"
+#include "sweep32.cuh"
 
 namespace llg {
 namespace {
@@ -52,140 +58,162 @@ struct TanParams {
     int n_k;            // samples in the window
 };
 
-__device__ __forceinline__ float3 nbr(const float4 *A, int q, int sy, int sz)
+// Neighbour indices of a cell in the compact layout, in the order x-, x+, y-, y+, z-, z+; `zero`
+// (the slot after the last cell) beyond a free face.
+struct Nbr {
+    int i[6];
+};
+
+__device__ __forceinline__ Nbr neighbours(int c, int nx, int ny, int nz, int zero)
 {
-    float3 nb = add3(xyz(A[q - 1]), xyz(A[q + 1]));
-    nb = add3(nb, xyz(A[q - sy]));
-    nb = add3(nb, xyz(A[q + sy]));
-    nb = add3(nb, xyz(A[q - sz]));
-    return add3(nb, xyz(A[q + sz]));
+    const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny), sxy = nx * ny;
+    Nbr n;
+    n.i[0] = x > 0 ? c - 1 : zero;
+    n.i[1] = x < nx - 1 ? c + 1 : zero;
+    n.i[2] = y > 0 ? c - nx : zero;
+    n.i[3] = y < ny - 1 ? c + nx : zero;
+    n.i[4] = z > 0 ? c - sxy : zero;
+    n.i[5] = z < nz - 1 ? c + sxy : zero;
+    return n;
 }
 
-// Three groups of warps per rod: group j carries the tangent dm/dtheta_j (threads g*TPG ..
-// g*TPG + TPG - 1, TPG = the rod's cells rounded up to a warp), and every group recomputes the
-// primal with the same arithmetic (so all three hold bitwise the same m); group 0 writes the
-// primal state to shared memory, group j its tangent.  Each thread's dependent chain is the
-// primal plus one tangent, and a rod has three times the warps to hide latency.
-// MAXT: the largest CTA of the instance (3 x 256 for rods up to 256 cells; 3 x 64 = 192 for the
-// smallest).
-template <bool AX, int MAXT>
-__global__ void __launch_bounds__(MAXT) tangent_kernel(TanParams tp, float *__restrict__ m_glob,
+// The neighbour sum in the order x-, x+, y-, y+, z-, z+ (every engine's order).
+__device__ __forceinline__ float3 nbr(const float4 *A, const Nbr &n)
+{
+    float3 nb = add3(xyz(A[n.i[0]]), xyz(A[n.i[1]]));
+    nb = add3(nb, xyz(A[n.i[2]]));
+    nb = add3(nb, xyz(A[n.i[3]]));
+    nb = add3(nb, xyz(A[n.i[4]]));
+    return add3(nb, xyz(A[n.i[5]]));
+}
+
+// CPT cells per thread (cell c + k * blockDim.x, k < CPT); MAXT the largest CTA of the instance;
+// SHAPE the sweep shape with 32-bit bookkeeping (0 triangle, 1 cosine), or -1 for the 64-bit sweep
+// of any period.  Each thread's dependent chain is the primal plus one tangent.
+template <bool AX, int CPT, int MAXT, int SHAPE>
+__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 1 : 0) tangent_kernel(TanParams tp, float *__restrict__ m_glob,
                                                       float *__restrict__ samples, float *__restrict__ dsamples,
                                                       int *__restrict__ status)
 {
     extern __shared__ float4 sm4[];
     const KParams &p = tp.p;
     const TanCoeffs &d = tp.d;
-    const int px = p.nx + 2, py = p.ny + 2;
-    const int sy = px, sz = px * py;
-    const int rod_pad = sz * (p.nz + 2);
-    // state and predictor, each as m and the three tangents
-    float4 *M = sm4, *P = sm4 + 4 * rod_pad;
-    const int rod = blockIdx.x;
     const int ncell = p.ncells;
-    const int tpg = blockDim.x / 3;            // threads per group (a multiple of 32)
-    const int grp = threadIdx.x / tpg;         // the tangent this thread carries (warp-uniform)
-    const int c = threadIdx.x - grp * tpg;
-    const bool act = c < ncell;
-    for (int i = threadIdx.x; i < 8 * rod_pad; i += blockDim.x) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    int q = 0;
-    if (act) {
-        const int x = c % p.nx, y = (c / p.nx) % p.ny, z = c / (p.nx * p.ny);
-        q = (x + 1) + sy * (y + 1) + sz * (z + 1);
-    }
+    const int S = ncell + 1;  // cells and the zero slot
+    // state m, its tangent, predictor, its tangent
+    float4 *M = sm4, *Md = sm4 + S, *P = sm4 + 2 * S, *Pd = sm4 + 3 * S;
+    const int rod = blockIdx.x, j = blockIdx.y;  // j: the parameter whose tangent this CTA carries
+    for (int i = threadIdx.x; i < 4 * S; i += blockDim.x) sm4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t real = p.real0 + (uint32_t)rod;
-    // this group's coefficient derivatives (a uniform index into the parameter block)
-    const float dcex = d.dcex[grp], dcan = d.dcan[grp], dalpha = d.dalpha[grp], da = d.da[grp],
-                rsig = d.rsig[grp];
-    float4 *Md = M + (grp + 1) * rod_pad, *Pd = P + (grp + 1) * rod_pad;
-    float3 m = zr3(), dm = zr3();  // the tangent starts at zero: m0 is fixed
-    if (act) m = make_float3(m_glob[((size_t)rod * ncell + c) * 3], m_glob[((size_t)rod * ncell + c) * 3 + 1],
-                             m_glob[((size_t)rod * ncell + c) * 3 + 2]);
-    float3 u = make_float3(0.f, 0.f, 1.f);
-    if (AX && act) u = xyz(__ldg(p.axis + (size_t)rod * ncell + c));
+    const PhiloxKeys keys = philox_keys(p.seed, real);  // the rod's round keys, formed once
+    // this CTA's coefficient derivatives (a uniform index into the parameter block)
+    const float dcex = d.dcex[j], dcan = d.dcan[j], dalpha = d.dalpha[j], da = d.da[j], rsig = d.rsig[j];
+    Nbr nb[CPT];
+    float3 m[CPT], dm[CPT], u[CPT], hpre[CPT];  // the tangent starts at zero: m0 is fixed
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        const int c = threadIdx.x + k * blockDim.x;
+        nb[k] = neighbours(0, p.nx, p.ny, p.nz, ncell);
+        m[k] = dm[k] = hpre[k] = zr3();
+        u[k] = make_float3(0.f, 0.f, 1.f);
+        if (c < ncell) {
+            nb[k] = neighbours(c, p.nx, p.ny, p.nz, ncell);
+            const float *src = m_glob + ((size_t)rod * ncell + c) * 3;
+            m[k] = make_float3(src[0], src[1], src[2]);
+            if (AX) u[k] = xyz(__ldg(p.axis + (size_t)rod * ncell + c));
+            // thermal field of the next step, drawn before the step's last barrier
+            hpre[k] = thermal_field(keys, (uint32_t)c, (unsigned long long)tp.step0, p.sigma);
+        }
+    }
     __syncthreads();
-    if (act && grp == 0) M[q] = pad4(m);
+#pragma unroll
+    for (int k = 0; k < CPT; ++k)
+        if (threadIdx.x + k * blockDim.x < ncell) M[threadIdx.x + k * blockDim.x] = pad4(m[k]);
     __syncthreads();
     const float alpha = p.alpha, a = -p.neg_dt_g1;
-    const int lane = threadIdx.x & 31, wig = c >> 5;  // lane, warp within the group
-    Sweep field;
+    const int lane = threadIdx.x & 31;
+    typename SweepSel<SHAPE>::type field;
     field.init(tp.step0, p);
     float Hn = field.value();
+    // steps to the next sample (32-bit countdown; the host keeps sample_every below 2^31)
+    const long long se = p.sample_every;
+    long long k_next = se > 0 ? tp.step0 / se + 1 : 0;
+    int to_sample = se > 0 ? (int)(k_next * se - tp.step0) : -1;
     // the field-tangent and torque-tangent of one half step: dH = dc_ex N + c_ex Nd + rsig h +
     // the anisotropy tangent; ds = dc + dalpha m x c + alpha (dm x c + m x dc), dc = dm x H + m x dH
-    auto half_tan = [&](float3 mm, float3 dmm, float3 N, float3 Nd, float3 h, float3 H, float3 *dsv) {
+    auto half_tan = [&](float3 mm, float3 dmm, float3 N, float3 Nd, float3 h, float3 H, float3 uu) {
         float3 dH = add3(sc3(dcex, N), sc3(p.c_ex, Nd));
         dH = add3(dH, sc3(rsig, h));
         if constexpr (AX) {
-            const float mu = dt3(mm, u), dmu = dt3(dmm, u);
-            dH = add3(dH, sc3(fmaf(dcan, mu, p.c_an * dmu), u));
+            const float mu = dt3(mm, uu), dmu = dt3(dmm, uu);
+            dH = add3(dH, sc3(fmaf(dcan, mu, p.c_an * dmu), uu));
         } else {
             dH.z = fmaf(dcan, mm.z, fmaf(p.c_an, dmm.z, dH.z));
         }
         const float3 cc = crs(mm, H);
         const float3 dc = add3(crs(dmm, H), crs(mm, dH));
-        *dsv = add3(add3(dc, sc3(dalpha, crs(mm, cc))), sc3(alpha, add3(crs(dmm, cc), crs(mm, dc))));
+        return add3(add3(dc, sc3(dalpha, crs(mm, cc))), sc3(alpha, add3(crs(dmm, cc), crs(mm, dc))));
     };
-    float3 hpre = zr3();  // thermal field of the next step, drawn before the step's last barrier
-    if (act) hpre = thermal_field(p.seed, real, (uint32_t)c, (unsigned long long)tp.step0, p.sigma);
     for (int s = 0; s < tp.n_steps; ++s) {
         const unsigned long long n = (unsigned long long)(tp.step0 + s);
         field.inc();
         const float Hn1 = field.value();
-        float3 acc = zr3(), dacc = zr3(), h = hpre, t = zr3(), dtt = zr3();
-        if (act) {
-            const float3 N = nbr(M, q, sy, sz), Nd = nbr(Md, q, sy, sz);
-            const float3 H = effective_field_sel<AX>(N, m, h, p, Hn, u);
-            const float3 s0 = llg_torque(m, H, alpha);
-            float3 ds0;
-            half_tan(m, dm, N, Nd, h, H, &ds0);
-            const float3 pv = axpy(p.neg_dt_g1, s0, m);
+        float3 acc[CPT], dacc[CPT], t[CPT], dtt[CPT];
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            acc[k] = dacc[k] = t[k] = dtt[k] = zr3();
+            const int c = threadIdx.x + k * blockDim.x;
+            if (c >= ncell) continue;
+            const float3 N = nbr(M, nb[k]), Nd = nbr(Md, nb[k]);
+            const float3 H = effective_field_sel<AX>(N, m[k], hpre[k], p, Hn, u[k]);
+            const float3 s0 = llg_torque(m[k], H, alpha);
+            const float3 ds0 = half_tan(m[k], dm[k], N, Nd, hpre[k], H, u[k]);
+            const float3 pv = axpy(p.neg_dt_g1, s0, m[k]);
             const float r = rsqrtf(fmaf(pv.x, pv.x, fmaf(pv.y, pv.y, pv.z * pv.z)));
-            t = make_float3(pv.x * r, pv.y * r, pv.z * r);  // normalised(pv), the engines' arithmetic
-            acc = axpy(p.neg_hdt_g1, s0, m);
-            const float3 dp = sb3(sb3(dm, sc3(da, s0)), sc3(a, ds0));
-            dtt = sc3(r, sb3(dp, sc3(dt3(t, dp), t)));
-            dacc = sb3(sb3(dm, sc3(0.5f * da, s0)), sc3(0.5f * a, ds0));
-            Pd[q] = pad4(dtt);
-            if (grp == 0) P[q] = pad4(t);
+            t[k] = make_float3(pv.x * r, pv.y * r, pv.z * r);  // normalised(pv), the engines' arithmetic
+            acc[k] = axpy(p.neg_hdt_g1, s0, m[k]);
+            const float3 dp = sb3(sb3(dm[k], sc3(da, s0)), sc3(a, ds0));
+            dtt[k] = sc3(r, sb3(dp, sc3(dt3(t[k], dp), t[k])));
+            dacc[k] = sb3(sb3(dm[k], sc3(0.5f * da, s0)), sc3(0.5f * a, ds0));
+            Pd[c] = pad4(dtt[k]);
+            P[c] = pad4(t[k]);
         }
         __syncthreads();
-        if (act) {
-            const float3 N = nbr(P, q, sy, sz), Nd = nbr(Pd, q, sy, sz);
-            const float3 H = effective_field_sel<AX>(N, t, h, p, Hn1, u);
-            const float3 s1 = llg_torque(t, H, alpha);
-            float3 ds1;
-            half_tan(t, dtt, N, Nd, h, H, &ds1);
-            const float3 qv = axpy(p.neg_hdt_g1, s1, acc);
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            const int c = threadIdx.x + k * blockDim.x;
+            if (c >= ncell) continue;
+            const float3 N = nbr(P, nb[k]), Nd = nbr(Pd, nb[k]);
+            const float3 H = effective_field_sel<AX>(N, t[k], hpre[k], p, Hn1, u[k]);
+            const float3 s1 = llg_torque(t[k], H, alpha);
+            const float3 ds1 = half_tan(t[k], dtt[k], N, Nd, hpre[k], H, u[k]);
+            const float3 qv = axpy(p.neg_hdt_g1, s1, acc[k]);
             const float r = rsqrtf(fmaf(qv.x, qv.x, fmaf(qv.y, qv.y, qv.z * qv.z)));
-            m = make_float3(qv.x * r, qv.y * r, qv.z * r);
-            const float3 dq = sb3(sb3(dacc, sc3(0.5f * da, s1)), sc3(0.5f * a, ds1));
-            dm = sc3(r, sb3(dq, sc3(dt3(m, dq), m)));
-            Md[q] = pad4(dm);
-            if (grp == 0) M[q] = pad4(m);
-            hpre = thermal_field(p.seed, real, (uint32_t)c, n + 1, p.sigma);
+            m[k] = make_float3(qv.x * r, qv.y * r, qv.z * r);
+            const float3 dq = sb3(sb3(dacc[k], sc3(0.5f * da, s1)), sc3(0.5f * a, ds1));
+            dm[k] = sc3(r, sb3(dq, sc3(dt3(m[k], dq), m[k])));
+            Md[c] = pad4(dm[k]);
+            M[c] = pad4(m[k]);
+            hpre[k] = thermal_field(keys, (uint32_t)c, n + 1, p.sigma);
         }
         __syncthreads();
         Hn = Hn1;
-        const long long done = (long long)n + 1;
-        if (p.sample_every > 0 && done % p.sample_every == 0) {
-            const long long kk = done / p.sample_every - tp.k_first;
-            if (kk >= 0 && kk < tp.n_k && wig == 0) {
-                // the first warp of each group: the canonical reduction of m_z (group 0, as every
-                // engine) or of its tangent's z component
-                const float4 *A = grp == 0 ? M : Md;
+        if (--to_sample == 0) {
+            to_sample = (int)se;
+            const long long kk = k_next++ - tp.k_first;
+            if (kk >= 0 && kk < tp.n_k && threadIdx.x < 32) {
+                // the first warp: the canonical reduction of m_z (every engine's) and of the
+                // tangent's z component
                 float part = 0.f, pd = 0.f;
                 for (int cc = lane; cc < ncell; cc += 32) {
-                    const int x = cc % p.nx, y = (cc / p.nx) % p.ny, z = cc / (p.nx * p.ny);
-                    const int qq = (x + 1) + sy * (y + 1) + sz * (z + 1);
-                    pd += Md[qq].z;
-                    if (grp == 0) part += A[qq].z;
+                    pd += Md[cc].z;
+                    part += M[cc].z;
                 }
                 const float dmean = warp_cell_mean(pd, ncell);
-                const float mean = grp == 0 ? warp_cell_mean(part, ncell) : 0.f;
+                const float mean = warp_cell_mean(part, ncell);
                 if (lane == 0) {
-                    dsamples[((size_t)rod * tp.n_k + kk) * 3 + grp] = dmean;
-                    if (grp == 0) {
+                    dsamples[((size_t)rod * tp.n_k + kk) * 3 + j] = dmean;
+                    if (j == 0) {
                         samples[(size_t)rod * tp.n_k + kk] = mean;
                         if (!isfinite(mean)) atomicOr(status, 1);
                     }
@@ -201,15 +229,15 @@ bool tangent_supported(const KParams &p, int dev)
 {
     int smem_optin = 0;
     if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
-    const size_t rod_pad = (size_t)(p.nx + 2) * (p.ny + 2) * (p.nz + 2);
-    return p.periodic == 0 && p.ncells <= 256 && 8 * rod_pad * sizeof(float4) <= (size_t)smem_optin;
+    return p.periodic == 0 && p.ncells <= 1408 && 4 * (size_t)(p.ncells + 1) * sizeof(float4) <= (size_t)smem_optin;
 }
 
 cudaError_t tangent_forward(const KParams &p, const double dcoef[15], int n_real, long long step0, long long n_steps,
                             long long k_first, int n_k, float *m_work, float *samples, float *dsamples, int *status,
                             cudaStream_t st)
 {
-    if (n_steps < 0 || n_steps > 0x7fffffffLL || n_k < 1) return cudaErrorInvalidValue;
+    if (n_steps < 0 || n_steps > 0x7fffffffLL || n_k < 1 || n_real < 1 || p.sample_every >= (1LL << 31))
+        return cudaErrorInvalidValue;
     TanParams tp;
     tp.p = p;
     for (int j = 0; j < 3; ++j) {
@@ -223,17 +251,26 @@ cudaError_t tangent_forward(const KParams &p, const double dcoef[15], int n_real
     tp.n_steps = (int)n_steps;
     tp.k_first = k_first;
     tp.n_k = n_k;
-    const size_t rod_pad = (size_t)(p.nx + 2) * (p.ny + 2) * (p.nz + 2);
-    const size_t smem = 8 * rod_pad * sizeof(float4);
-    const int threads = 3 * ((p.ncells + 31) / 32 * 32);  // three groups, one per tangent
-    auto go = [&](auto kern) {
+    const size_t smem = 4 * (size_t)(p.ncells + 1) * sizeof(float4);
+    const dim3 grid((unsigned)n_real, 3);
+    auto go = [&](auto kern, int threads) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<n_real, threads, smem, st>>>(tp, m_work, samples, dsamples, status);
+        kern<<<grid, threads, smem, st>>>(tp, m_work, samples, dsamples, status);
         return cudaGetLastError();
     };
-    if (threads <= 3 * 64) return p.axis ? go(tangent_kernel<true, 192>) : go(tangent_kernel<false, 192>);
-    if (threads <= 3 * 256) return p.axis ? go(tangent_kernel<true, 768>) : go(tangent_kernel<false, 768>);
+    const int t1 = (p.ncells + 31) / 32 * 32;             // one cell per thread
+    const int t2 = ((p.ncells + 1) / 2 + 31) / 32 * 32;   // two cells per thread
+    // the sweep shape at compile time where its period fits 32 bits
+    const int shape = sweep_fits_32(p) ? (p.shape == 1 ? 1 : 0) : -1;
+    auto by_shape = [&](auto k0, auto k1, auto kg, int threads) {
+        return shape == 0 ? go(k0, threads) : shape == 1 ? go(k1, threads) : go(kg, threads);
+    };
+#define LLG_TAN(AXV, C, T) tangent_kernel<AXV, C, T, 0>, tangent_kernel<AXV, C, T, 1>, tangent_kernel<AXV, C, T, -1>
+    if (t1 <= 192) return p.axis ? by_shape(LLG_TAN(true, 1, 192), t1) : by_shape(LLG_TAN(false, 1, 192), t1);
+    if (t1 <= 768) return p.axis ? by_shape(LLG_TAN(true, 1, 768), t1) : by_shape(LLG_TAN(false, 1, 768), t1);
+    if (t2 <= 704) return p.axis ? by_shape(LLG_TAN(true, 2, 704), t2) : by_shape(LLG_TAN(false, 2, 704), t2);
+#undef LLG_TAN
     return cudaErrorInvalidValue;
 }
 

@@ -173,7 +173,7 @@ cudaError_t adjoint_backward_all(const KParams &p, int n_real, long long step0, 
                                  int n_k, const float *states, float *lam, const double *w, double *partial,
                                  cudaStream_t st);
 
-// ---- tangent gradient (k_tangent.cu): one pass, one CTA per rod, rods of at most 1024 cells -----
+// ---- tangent gradient (k_tangent.cu): one pass, a CTA per rod and parameter, <= 1408 cells -----
 bool tangent_supported(const KParams &p, int dev);
 // dcoef: the derivatives of (c_ex, c_an, alpha, a = dt g1) and dsigma/sigma with respect to
 // (s_K, s_alpha, s_Ms), five groups of three.  m_work (advanced in place), samples [n_real][n_k]

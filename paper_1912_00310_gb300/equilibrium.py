@@ -13,7 +13,8 @@ GPU through the library's C ABI, the time-averaged magnetisation of
 in zero field from the saturated state, and prints each level's values beside the two
 statements: m_b(T0) against m_1(T(b)) (Eq. 12 read for the magnetisation) and m_1(T0) against
 (delta zeta + 1 - delta) m_b(T0) (Eq. 13), with the delta that would make Eq. 13 exact at that
-level.  The magnetisation is |<m_z>| of the cell average at each sample (the rod's moment stays
+level; and the delta of the M(T) fit (Fig. 3), where Eqs. 12 and 13 together give the unscaled
+rod's magnetisation at T(b) as m_1(T0) / (delta zeta + 1 - delta).  The magnetisation is |<m_z>| of the cell average at each sample (the rod's moment stays
 along its easy axis; its sign may flip at the coarser levels, whose anisotropy barrier is a few
 k_B T), averaged over the samples after the burn-in and then over realisations (standard error
 over realisations).
@@ -105,6 +106,7 @@ def main(argv=None):
                    m_rod_Tb_se=cold["m_se"], m_rod_T0=ref["m"], m_rod_T0_se=ref["m_se"],
                    eq12_ratio=lev["m"] / cold["m"], eq13_m0=f13 * lev["m"], eq13_ratio=f13 * lev["m"] / ref["m"],
                    delta_exact=(ref["m"] / lev["m"] - 1.0) / (z - 1.0) if z != 1.0 else None,
+                   delta_mt=(ref["m"] / cold["m"] - 1.0) / (z - 1.0) if z != 1.0 else None,
                    seconds=lev["seconds"] + cold["seconds"])
         print(json.dumps(out), flush=True)
 

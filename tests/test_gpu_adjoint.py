@@ -18,11 +18,11 @@ def pkg():
     return P
 
 
-def grid(pkg, dims, scale=(1.0, 1.0, 1.0), alpha=None):
-    g = pkg.Grid(*dims, a0=M["a0"], b=4)
+def grid(pkg, dims, scale=(1.0, 1.0, 1.0), alpha=None, b=4, dt=10e-15):
+    g = pkg.Grid(*dims, a0=M["a0"], b=b)
     g.set_material(A0=M["A0"], Ms=M["Ms"], K0=M["K0"], alpha=alpha or M["alpha"], T=M["T"])
     g.set_scaling(mode=1, Tc=M["Tc"], scale=scale)
-    g.set_sweep(H_start=1500.0, H_turn=-1500.0, rate=1000.0, dt=10e-15, sample_dH=1.0)
+    g.set_sweep(H_start=1500.0, H_turn=-1500.0, rate=1000.0, dt=dt, sample_dH=1.0)
     return g
 
 
@@ -30,12 +30,12 @@ def target_for(g):
     return 0.92 + 0.05 * np.cos(np.arange(g.n_samples) / 7.0)
 
 
-def oracle_grad(orc, dims, m0, scale, step0, n_steps, target, alpha=None, seed=0):
-    p = orc.material_problem(*dims, a0=M["a0"], b=4, A0=M["A0"], K0=M["K0"], Ms=M["Ms"],
-                             alpha=alpha or M["alpha"], T=M["T"], dt=10e-15, mode=1, Tc=M["Tc"],
+def oracle_grad(orc, dims, m0, scale, step0, n_steps, target, alpha=None, seed=0, b=4, dt=10e-15):
+    p = orc.material_problem(*dims, a0=M["a0"], b=b, A0=M["A0"], K0=M["K0"], Ms=M["Ms"],
+                             alpha=alpha or M["alpha"], T=M["T"], dt=dt, mode=1, Tc=M["Tc"],
                              H_start_Oe=1500.0, H_turn_Oe=-1500.0, rate_Oe_per_ns=1000.0)
     return orc.loss_grad(p, m0, target=target, scale=scale, seed=seed, step0=step0,
-                         n_steps=n_steps, sample_every=100)
+                         n_steps=n_steps, sample_every=orc.sample_interval(1.0, 1000.0, dt))
 
 
 @pytest.mark.parametrize("scale,alpha", [((1.0, 1.0, 1.0), None), ((1.25, 0.8, 1.1), 0.5)])
@@ -210,4 +210,26 @@ def test_tangent_method_matches_adjoint_and_oracle(pkg, orc, disp, shape):
         assert out[1][0] == pytest.approx(Lo, rel=1e-3)
         for k in range(3):
             assert out[1][1][k] == pytest.approx(go[k], rel=1e-2), (k, out[1][1], go)
+    g.close()
+
+
+def test_tangent_method_b2_rod_vs_oracle(pkg, orc):
+    """The b = 2 rod (4 x 12 x 28 = 1344 cells, beyond the adjoint's one cell per thread): the
+    tangent method (two cells per thread) against the FP64 forward-mode oracle gradient, within
+    1e-2 relative with no absolute floor, and its loss against the oracle's."""
+    dims, n_real, n_steps, dt = ROD_DIMS[2], 8, 3000, 5e-15
+    g = grid(pkg, dims, b=2, dt=dt)
+    g.set_tuning(pkg.TUNE_GRAD_METHOD, 1)
+    g.reset(seed=4, n_real=n_real)
+    target = target_for(g)
+    L, grad = g.loss_grad(n_steps, target, 0, 256)
+    assert g.step == 0
+    m0 = orc.uniform_state(n_real, g.ncells)
+    Lo, go, _ = oracle_grad(orc, dims, m0, (1.0, 1.0, 1.0), 0, n_steps, target, seed=4, b=2, dt=dt)
+    assert L == pytest.approx(Lo, rel=1e-3)
+    for k in range(3):
+        assert grad[k] == pytest.approx(go[k], rel=1e-2), (k, grad, go)
+    g.set_tuning(pkg.TUNE_GRAD_METHOD, 0)
+    with pytest.raises(pkg.LLGError):
+        g.loss_grad(n_steps, target, 0, 256)  # the adjoint stops at 1024 cells
     g.close()
