@@ -233,3 +233,34 @@ def test_tangent_method_b2_rod_vs_oracle(pkg, orc):
     with pytest.raises(pkg.LLGError):
         g.loss_grad(n_steps, target, 0, 256)  # the adjoint stops at 1024 cells
     g.close()
+
+
+def test_gradient_methods_long_period_sweep(pkg, orc):
+    """A triangle sweep whose period exceeds 2^31 steps (500 -> -500 Oe at 0.05 Oe/ns, 10 fs) runs
+    the gradient kernels' instances with the 64-bit sweep phase: the adjoint and the tangent method
+    agree with the FP64 forward-mode oracle gradient within 1e-2 and with each other within 1e-3."""
+    dims, n_real, n_steps, dt = (1, 2, 3), 16, 12000, 10e-15
+    g = pkg.Grid(*dims, a0=M["a0"], b=4)
+    g.set_material(A0=M["A0"], Ms=M["Ms"], K0=M["K0"], alpha=0.5, T=M["T"])
+    g.set_scaling(mode=1, Tc=M["Tc"])
+    g.set_sweep(H_start=500.0, H_turn=-500.0, rate=0.05, dt=dt, sample_dH=2e-3)
+    assert g.steps_per_loop >= 2 ** 31
+    target = 0.92 + 0.05 * np.cos(np.arange(g.n_samples) / 7.0)
+    out = {}
+    for method in (0, 1):
+        g.set_tuning(pkg.TUNE_GRAD_METHOD, method)
+        g.reset(seed=9, n_real=n_real)
+        out[method] = g.loss_grad(n_steps, target, 0, 4096)
+    assert out[0][0] == out[1][0]
+    p = orc.material_problem(*dims, a0=M["a0"], b=4, A0=M["A0"], K0=M["K0"], Ms=M["Ms"], alpha=0.5,
+                             T=M["T"], dt=dt, mode=1, Tc=M["Tc"], H_start_Oe=500.0, H_turn_Oe=-500.0,
+                             rate_Oe_per_ns=0.05)
+    Lo, go, _ = orc.loss_grad(p, orc.uniform_state(n_real, g.ncells), target=target, seed=9, step0=0,
+                              n_steps=n_steps, sample_every=orc.sample_interval(2e-3, 0.05, dt))
+    assert out[1][0] == pytest.approx(Lo, rel=1e-3)
+    for method in (0, 1):
+        for k in range(3):
+            assert out[method][1][k] == pytest.approx(go[k], rel=1e-2, abs=1e-3 * np.abs(go).max()), \
+                (method, k, out[method][1], go)
+    assert np.allclose(out[1][1], out[0][1], rtol=1e-3, atol=1e-4 * np.abs(go).max())
+    g.close()

@@ -413,3 +413,24 @@ def test_held_field_samples_and_time_average(pkg, orc):
         swept.set_sweep(H_start=100.0, H_turn=-100.0, rate=1000.0, dt=20e-15, sample_dH=1.0)
         swept.set_held_samples(10)
     g.close()
+
+
+def test_resumable_protocol_run_equals_uninterrupted(pkg, tmp_path):
+    """A level's loops run in chunks, the ensemble saved to a checkpoint and restored between
+    calls (protocol.run_resumable), give bitwise the observables of one uninterrupted run: the
+    noise and the field depend on the absolute step only."""
+    from paper_1912_00310_gb300 import protocol as P
+    kw = dict(rate=10.0, dt=20e-15)  # b = 8: a cycle of 1e7 steps, a sample every 5000; it switches
+    ck = str(tmp_path / "b8.npz")
+    r1 = P.run_resumable(8, 64, 3, ck, max_chunks=2, chunk=1 << 18, **kw)
+    assert r1["unfinished"] and r1["step"] == 2 << 18
+    with pytest.raises(ValueError):
+        P.run_resumable(8, 32, 3, ck, max_chunks=1, chunk=1 << 18, **kw)  # another ensemble
+    r2 = P.run_resumable(8, 64, 3, ck, chunk=1 << 18, **kw)
+    assert not r2.get("unfinished") and r2["samples_finite"]
+    assert not (tmp_path / "b8.npz").exists()
+    ref = P.run(8, 64, 3, tune=False, **kw)
+    assert math.isfinite(ref["Hc_Oe"]) and ref["area_Oe"] > 0
+    for k in ("Hc_Oe", "Hc_se_Oe", "area_Oe", "area_se_Oe", "area0_Oe", "Hc_down_Oe", "Hc_up_Oe"):
+        same = r2[k] == ref[k] or (math.isnan(r2[k]) and math.isnan(ref[k]))
+        assert same, (k, r2[k], ref[k])
