@@ -34,19 +34,19 @@
 
 #include "llg_internal.h"
 #include "physics.cuh"
+#include "rod_compact.cuh"
 #include "sweep32.cuh"
 
 namespace llg {
 namespace {
 
-__device__ __forceinline__ float3 cross3(float3 a, float3 b)
-{
-    return make_float3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
-}
-__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
-__device__ __forceinline__ float3 scale3(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
-__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ float3 zero3a() { return make_float3(0.f, 0.f, 0.f); }
+using grad::cross3;
+using grad::dot3;
+using grad::scale3;
+using grad::sub3;
+using grad::Nbr;
+using grad::neighbours;
+__device__ __forceinline__ float3 zero3a() { return grad::zero3(); }
 
 constexpr long long kAdjBlock = 64;  // steps per FP32 block of the parameter partial sums
 
@@ -63,37 +63,6 @@ struct AdjParams {
                           // steps after seg_start (its checkpoint and states offset to match)
     long long n_total;    // ... and the window has n_total steps (the last segment is shorter)
 };
-
-// The rod in shared memory is compact: one float4 per cell in cell order plus one zero slot that
-// stands for every neighbour beyond a free face, so that consecutive threads read consecutive
-// float4s (a ghost-padded layout of a thin rod leaves most banks of each row unused and every
-// neighbour load conflicted).  Neighbour indices of a cell in the order x-, x+, y-, y+, z-, z+.
-struct Nbr {
-    int i[6];
-};
-
-__device__ __forceinline__ Nbr neighbours(int c, int nx, int ny, int nz, int zero)
-{
-    const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny), sxy = nx * ny;
-    Nbr n;
-    n.i[0] = x > 0 ? c - 1 : zero;
-    n.i[1] = x < nx - 1 ? c + 1 : zero;
-    n.i[2] = y > 0 ? c - nx : zero;
-    n.i[3] = y < ny - 1 ? c + nx : zero;
-    n.i[4] = z > 0 ? c - sxy : zero;
-    n.i[5] = z < nz - 1 ? c + sxy : zero;
-    return n;
-}
-
-// Neighbour sum over the six faces (x-, x+, y-, y+, z-, z+), every engine's order.
-__device__ __forceinline__ float3 nsum(const float4 *A, const Nbr &n)
-{
-    float3 nb = add3(xyz(A[n.i[0]]), xyz(A[n.i[1]]));
-    nb = add3(nb, xyz(A[n.i[2]]));
-    nb = add3(nb, xyz(A[n.i[3]]));
-    nb = add3(nb, xyz(A[n.i[4]]));
-    return add3(nb, xyz(A[n.i[5]]));
-}
 
 // MAXT: the largest CTA the instance runs with (256 for rods up to 256 cells, which then get up to
 // 255 registers per thread, 1024 otherwise); SHAPE: the sweep shape with 32-bit bookkeeping (0
@@ -157,7 +126,7 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
         __syncthreads();
         if (act) {
             h = thermal_field(keys, (uint32_t)c, n, p.sigma);
-            const float3 H = field_of(nsum(M, nb), m, h, Hn);
+            const float3 H = field_of(grad::neighbour_sum(M, nb), m, h, Hn);
             const float3 s0 = llg_torque(m, H, p.alpha);
             P[q] = pad4(normalised(axpy(p.neg_dt_g1, s0, m)));
             acc = axpy(p.neg_hdt_g1, s0, m);
@@ -165,7 +134,7 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
         __syncthreads();
         if (act) {
             const float3 t = xyz(P[q]);
-            const float3 H = field_of(nsum(P, nb), t, h, Hn1);
+            const float3 H = field_of(grad::neighbour_sum(P, nb), t, h, Hn1);
             m = normalised(axpy(p.neg_hdt_g1, llg_torque(t, H, p.alpha), acc));
         }
         __syncthreads();
@@ -240,7 +209,7 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
         float3 Nm = zero3a();
         if (act) {
             h = thermal_field(keys, (uint32_t)c, (unsigned long long)n, p.sigma);
-            Nm = nsum(M, nb);
+            Nm = grad::neighbour_sum(M, nb);
             H = field_of(Nm, mi, h, hn);
             c0 = cross3(mi, H);
             s0 = llg_torque(mi, H, alpha);
@@ -253,7 +222,7 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
         float3 gHt = zero3a(), Nt = zero3a(), c1 = zero3a(), gq = zero3a(), gmt = zero3a(), Ht = zero3a();
         float3 s1 = zero3a();
         if (act) {
-            Nt = nsum(P, nb);
+            Nt = grad::neighbour_sum(P, nb);
             Ht = field_of(Nt, t, h, hn1);
             c1 = cross3(t, Ht);
             s1 = llg_torque(t, Ht, alpha);
@@ -272,7 +241,7 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
         __syncthreads();
         float3 gH = zero3a(), gm = zero3a();
         if (act) {
-            gmt = axpy(p.c_ex, nsum(GT, nb), gmt);
+            gmt = axpy(p.c_ex, grad::neighbour_sum(GT, nb), gmt);
             if constexpr (AX) {
                 const float gu = dot3(gHt, u);
                 gmt = axpy(p.c_an * gu, u, gmt);
@@ -296,7 +265,7 @@ __global__ void __launch_bounds__(MAXT) adjoint_segment_kernel(
         }
         __syncthreads();
         if (act) {
-            gm = axpy(p.c_ex, nsum(GH, nb), gm);
+            gm = axpy(p.c_ex, grad::neighbour_sum(GH, nb), gm);
             if constexpr (AX) {
                 const float gu = dot3(gH, u);
                 gm = axpy(p.c_an * gu, u, gm);

@@ -30,19 +30,19 @@
 #include "llg_internal.h"
 #include "physics.cuh"
 #include "reduce.cuh"
+#include "rod_compact.cuh"
 #include "sweep32.cuh"
 
 namespace llg {
 namespace {
 
-__device__ __forceinline__ float3 zr3() { return make_float3(0.f, 0.f, 0.f); }
-__device__ __forceinline__ float3 crs(float3 a, float3 b)
-{
-    return make_float3(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
-}
-__device__ __forceinline__ float dt3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
-__device__ __forceinline__ float3 sc3(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
-__device__ __forceinline__ float3 sb3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+using grad::Nbr;
+using grad::neighbours;
+__device__ __forceinline__ float3 zr3() { return grad::zero3(); }
+__device__ __forceinline__ float3 crs(float3 a, float3 b) { return grad::cross3(a, b); }
+__device__ __forceinline__ float dt3(float3 a, float3 b) { return grad::dot3(a, b); }
+__device__ __forceinline__ float3 sc3(float s, float3 a) { return grad::scale3(s, a); }
+__device__ __forceinline__ float3 sb3(float3 a, float3 b) { return grad::sub3(a, b); }
 
 // Derivatives of the simulation coefficients with respect to theta_j at the current scale.
 struct TanCoeffs {
@@ -57,35 +57,6 @@ struct TanParams {
     long long k_first;  // first sample number of the window
     int n_k;            // samples in the window
 };
-
-// Neighbour indices of a cell in the compact layout, in the order x-, x+, y-, y+, z-, z+; `zero`
-// (the slot after the last cell) beyond a free face.
-struct Nbr {
-    int i[6];
-};
-
-__device__ __forceinline__ Nbr neighbours(int c, int nx, int ny, int nz, int zero)
-{
-    const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny), sxy = nx * ny;
-    Nbr n;
-    n.i[0] = x > 0 ? c - 1 : zero;
-    n.i[1] = x < nx - 1 ? c + 1 : zero;
-    n.i[2] = y > 0 ? c - nx : zero;
-    n.i[3] = y < ny - 1 ? c + nx : zero;
-    n.i[4] = z > 0 ? c - sxy : zero;
-    n.i[5] = z < nz - 1 ? c + sxy : zero;
-    return n;
-}
-
-// The neighbour sum in the order x-, x+, y-, y+, z-, z+ (every engine's order).
-__device__ __forceinline__ float3 nbr(const float4 *A, const Nbr &n)
-{
-    float3 nb = add3(xyz(A[n.i[0]]), xyz(A[n.i[1]]));
-    nb = add3(nb, xyz(A[n.i[2]]));
-    nb = add3(nb, xyz(A[n.i[3]]));
-    nb = add3(nb, xyz(A[n.i[4]]));
-    return add3(nb, xyz(A[n.i[5]]));
-}
 
 // CPT cells per thread (cell c + k * blockDim.x, k < CPT); MAXT the largest CTA of the instance;
 // SHAPE the sweep shape with 32-bit bookkeeping (0 triangle, 1 cosine), or -1 for the 64-bit sweep
@@ -164,7 +135,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 1 : 0) tangent_kernel(TanP
             acc[k] = dacc[k] = t[k] = dtt[k] = zr3();
             const int c = threadIdx.x + k * blockDim.x;
             if (c >= ncell) continue;
-            const float3 N = nbr(M, nb[k]), Nd = nbr(Md, nb[k]);
+            const float3 N = grad::neighbour_sum(M, nb[k]), Nd = grad::neighbour_sum(Md, nb[k]);
             const float3 H = effective_field_sel<AX>(N, m[k], hpre[k], p, Hn, u[k]);
             const float3 s0 = llg_torque(m[k], H, alpha);
             const float3 ds0 = half_tan(m[k], dm[k], N, Nd, hpre[k], H, u[k]);
@@ -183,7 +154,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 1 : 0) tangent_kernel(TanP
         for (int k = 0; k < CPT; ++k) {
             const int c = threadIdx.x + k * blockDim.x;
             if (c >= ncell) continue;
-            const float3 N = nbr(P, nb[k]), Nd = nbr(Pd, nb[k]);
+            const float3 N = grad::neighbour_sum(P, nb[k]), Nd = grad::neighbour_sum(Pd, nb[k]);
             const float3 H = effective_field_sel<AX>(N, t[k], hpre[k], p, Hn1, u[k]);
             const float3 s1 = llg_torque(t[k], H, alpha);
             const float3 ds1 = half_tan(t[k], dtt[k], N, Nd, hpre[k], H, u[k]);
