@@ -35,12 +35,16 @@
 
 namespace {
 
+// Autotuned launch shapes, keyed by what selects the kernel instances: the device, the grid, the
+// ensemble size, the sweep shape, whether the sweep and sample bookkeeping fit 32 bits, dispersed
+// axes and the periodic faces.
 struct TuneKey {
     std::string device;
-    int nx, ny, nz, n_real;
+    int nx, ny, nz, n_real, shape, fits32, axes, periodic;
     bool operator<(const TuneKey &o) const
     {
-        return std::tie(device, nx, ny, nz, n_real) < std::tie(o.device, o.nx, o.ny, o.nz, o.n_real);
+        return std::tie(device, nx, ny, nz, n_real, shape, fits32, axes, periodic) <
+               std::tie(o.device, o.nx, o.ny, o.nz, o.n_real, o.shape, o.fits32, o.axes, o.periodic);
     }
 };
 struct TuneValue {
@@ -125,11 +129,18 @@ extern "C" llg_status llg_autotune(llg_ctx *ctx, int64_t trial_steps, double *be
         llg::set_last_error("cudaGetDeviceProperties failed");
         return LLG_ECUDA;
     }
-    const TuneKey key{prop.name, v.kp.nx, v.kp.ny, v.kp.nz, v.n_real};
+    const long long period = v.kp.shape == 1 ? v.kp.period : 2 * v.kp.n_half;
+    const int fits32 = period < (1LL << 31) && v.kp.sample_every < (1LL << 31);
+    const TuneKey key{prop.name, v.kp.nx, v.kp.ny, v.kp.nz, v.n_real, v.kp.shape, fits32,
+                      v.kp.axis != nullptr, (int)v.kp.periodic};
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) {
+        llg::RodPlan check{};
+        // a cached shape is taken only while it still plans for this context
+        if (it != g_tune_cache.end() &&
+            (it->second.kind == 0 || llg::rod_plan(v.kp, v.n_real, v.device, &check, it->second.kind,
+                                                   it->second.rods, it->second.rows, it->second.cpt))) {
             llg_set_tuning(ctx, LLG_TUNE_ROD_KIND, it->second.kind);
             llg_set_tuning(ctx, LLG_TUNE_RODS_PER_CTA, it->second.rods);
             llg_set_tuning(ctx, LLG_TUNE_ROWS_PER_THREAD, it->second.rows);

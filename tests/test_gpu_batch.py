@@ -92,3 +92,25 @@ def test_autotune_keeps_the_ensemble(pkg):
         assert torch.equal(state(g, n), state(ref, n))  # the tuned shape computes the same
         g.close()
         ref.close()
+
+
+def test_autotune_cache_follows_the_sweep(pkg):
+    """Two b = 4 ensembles of the same size, one swept within 2^31 steps and one whose sweep
+    phase needs 64 bits (the +-1500 Oe loop at 0.1 Oe/ns): the second autotune does not reuse the
+    first's launch shape (the row kernel takes only 32-bit sweeps), and its ensemble then
+    advances bitwise like the plain engine's."""
+    n_real = 64
+    a = job(pkg, 4, 1000.0, 0.1, n_real, 0)
+    a.autotune(trial_steps=200)
+    b = job(pkg, 4, 0.1, 0.1, n_real, 0)
+    assert b.steps_per_loop >= 2 ** 31
+    b.autotune(trial_steps=200)
+    b.advance(300)
+    c = job(pkg, 4, 0.1, 0.1, n_real, 0)
+    c.set_engine(pkg.ENGINE_PLAIN)
+    c.advance(300)
+    sb, sc = state(b, n_real), state(c, n_real)
+    assert torch.isfinite(sb).all()
+    assert torch.equal(sb, sc)
+    for g in (a, b, c):
+        g.close()
