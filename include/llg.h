@@ -280,8 +280,10 @@ llg_status llg_run_batch(llg_ctx *const *jobs, int n_jobs, int64_t max_steps,
  * kernel) for trial_steps Heun steps each on a scratch copy of the ensemble (allocated and freed
  * here), and set them with llg_set_tuning; also set the steps per launch (LLG_TUNE_CHUNK_STEPS)
  * from the measured time of a one-step launch, so that the launch overhead stays near 1% of a
- * launch.  Results are cached per (device, grid, realisation count) for the life of the
- * process.  The ensemble itself is not advanced.  best_rate (optional) receives the fastest
+ * launch.  Results are cached for the life of the process per (device, grid, realisation
+ * count, sweep shape, whether the sweep and sample counts fit 32 bits, dispersed axes, periodic
+ * faces), and a cached shape is used only while it still plans for the context.  The ensemble
+ * itself is not advanced.  best_rate (optional) receives the fastest
  * cell-steps/s.  Synchronises.  Errors: EINVAL (no ensemble), ENOMEM, EUNSUPPORTED. */
 llg_status llg_autotune(llg_ctx *ctx, int64_t trial_steps, double *best_rate);
 
