@@ -160,3 +160,8 @@ def test_protocol_levels_and_loss_power():
         P.level_grid(3)
     # f mu0 (1000/4pi) Ms S / rho at 125 kHz: 198.8 W/g for the printed area (R13)
     assert P.specific_loss_power_W_per_g(171.3, 125e3) == pytest.approx(198.8, abs=0.05)
+    # a resumable run takes one level and one rate (refused before any device work)
+    for argv in (["--b", "1", "4", "--checkpoint", "x.npz"],
+                 ["--b", "4", "--rates", "2.5", "5", "--sr-over-alpha", "2.5", "--checkpoint", "x.npz"]):
+        with pytest.raises(SystemExit):
+            P.main(argv)
