@@ -344,8 +344,9 @@ llg_status llg_loop_stats_host(const float *m_samples, int n_real, int64_t n_sam
  * (one per GPU; the realisations of the loop paragraph are independent).  The exchange is two
  * small sums across processes:
  *   1. llg_loop_moments on each process: per-sample sums sum_out [n_samples] (and, optional,
- *      sums of squares sumsq_out) of its own realisations, in FP64; the processes add them and
- *      their realisation counts (n_total);
+ *      sums of squares sumsq_out) of its own realisations, in FP64 (zeros for a process holding
+ *      none: n_real 0, m_samples may be NULL); the processes add them and their realisation
+ *      counts (n_total);
  *   2. llg_loop_jackknife_terms on each process: given the global sums sum_all, the delete-one
  *      jackknife terms of its own n_local realisations, out = {sum d_Hc, sum d_Hc^2, sum d_area,
  *      sum d_area^2} with d = (statistic of the mean loop without that realisation) - (statistic

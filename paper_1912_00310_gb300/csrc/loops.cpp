@@ -99,8 +99,8 @@ double jackknife_se(double s1, double s2, int n)
 extern "C" llg_status llg_loop_moments(const float *m_samples, int n_real, int64_t n_samples, double *sum_out,
                                        double *sumsq_out)
 {
-    if (!m_samples || !sum_out || n_real < 1 || n_samples < 1) {
-        llg::set_last_error("need samples, n_real >= 1, n_samples >= 1 and an output array");
+    if (!sum_out || n_real < 0 || (n_real > 0 && !m_samples) || n_samples < 1) {
+        llg::set_last_error("need samples (unless n_real is 0), n_real >= 0, n_samples >= 1 and an output array");
         return LLG_EINVAL;
     }
     for (int64_t k = 0; k < n_samples; ++k) {

@@ -40,7 +40,8 @@ def sample_moments(samples: np.ndarray, group=None):
     s = np.ascontiguousarray(samples, dtype=np.float32)
     n_local, n = s.shape
     buf = np.zeros(2 * n + 1)
-    _lib.check(L.llg_loop_moments(s.ctypes.data, n_local, n, _dp(buf[:n]), _dp(buf[n:2 * n])))
+    _lib.check(L.llg_loop_moments(s.ctypes.data if n_local else None, n_local, n, _dp(buf[:n]),
+                                  _dp(buf[n:2 * n])))
     buf[2 * n] = n_local
     tot = _allreduce_sum(buf, group)
     return int(round(tot[2 * n])), tot[:n], tot[n:2 * n]

@@ -59,12 +59,12 @@ def _loop_samples():
     return H, n_half, S
 
 
-def _stats_worker(rank, world, port, out):
+def _stats_worker(rank, world, port, out, split):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     from paper_1912_00310_gb300 import ensemble
     H, n_half, S = _loop_samples()
-    mine = S[:7] if rank == 0 else S[7:]  # uneven split
+    mine = S[:split] if rank == 0 else S[split:]  # uneven split (split 0: rank 0 holds none)
     d = ensemble.loop_stats(mine, H, n_half, mode=1, zeta=0.81935)
     out[rank] = {k: d[k] for k in ("Hc_Oe", "Hc_se_Oe", "area_Oe", "area_se_Oe", "area0_Oe", "n_real")}
     out[f"mean{rank}"] = d["mean"].tolist()
@@ -73,7 +73,8 @@ def _stats_worker(rank, world, port, out):
     dist.destroy_process_group()
 
 
-def test_loop_statistics_over_two_ranks():
+@pytest.mark.parametrize("split", [7, 0])
+def test_loop_statistics_over_two_ranks(split):
     import numpy as np
     from paper_1912_00310_gb300 import build
     build.build()
@@ -81,7 +82,7 @@ def test_loop_statistics_over_two_ranks():
     port = _free_port()
     with mp.Manager() as mgr:
         out = mgr.dict()
-        mp.spawn(_stats_worker, args=(2, port, out), nprocs=2, join=True)
+        mp.spawn(_stats_worker, args=(2, port, out, split), nprocs=2, join=True)
         res = dict(out)
     H, n_half, S = _loop_samples()
     ref = P.loop_stats(S, H, n_half, mode=1, zeta=0.81935)
