@@ -43,13 +43,23 @@ def _current_stream(device: int):
     return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
+def _current_device() -> int:
+    """The caller's current CUDA device (torch's), 0 without one: a process that drives one GPU
+    of several (one rank per GPU) gets its contexts, streams and buffers on the same device."""
+    import torch
+    return torch.cuda.current_device() if torch.cuda.is_available() else 0
+
+
 class Grid:
-    """One grid of nx*ny*nz cubic cells of edge b*a0 (context of the C ABI)."""
+    """One grid of nx*ny*nz cubic cells of edge b*a0 (context of the C ABI), on `device` (default:
+    the current CUDA device) and `stream` (default: that device's current torch stream)."""
 
     def __init__(self, nx: int, ny: int, nz: int, *, a0: float, b: int = 1, periodic: int = 0,
-                 device: int = 0, stream=None):
+                 device: int | None = None, stream=None):
         L = _lib.load()
         self._L = L
+        if device is None:
+            device = _current_device()
         h = C.c_void_p()
         st = stream if stream is not None else _current_stream(device)
         _lib.check(L.llg_create_grid(C.byref(h), nx, ny, nz, a0, b, periodic, device, st))
@@ -276,10 +286,11 @@ def specific_loss_power(f_hz: float, Ms: float, area_Oe: float, rho_kg_m3: float
     return out.value
 
 
-def measure_alu_peak(device: int = 0) -> dict:
-    """Measured 32-bit lane issue rates of the GPU (llg_measure_alu_peak)."""
+def measure_alu_peak(device: int | None = None) -> dict:
+    """Measured 32-bit lane issue rates of the GPU (llg_measure_alu_peak; default: the current
+    CUDA device)."""
     out = (C.c_double * 4)()
-    _lib.check(_lib.load().llg_measure_alu_peak(device, out))
+    _lib.check(_lib.load().llg_measure_alu_peak(_current_device() if device is None else device, out))
     return dict(ffma_lane_ops_per_s=out[0], ffma_sm_mhz=out[1], int_lane_ops_per_s=out[2],
                 int_sm_mhz=out[3])
 

@@ -35,7 +35,7 @@ ROD_CELLS = (8, 24, 56)
 DT_BY_B = {1: 2e-15, 2: 5e-15, 4: 10e-15, 8: 20e-15}
 
 
-def make_grid(b: int, T: float, *, H_Oe=0.0, sample_every=100, device=0, stream=None, engine=ENGINE_AUTO,
+def make_grid(b: int, T: float, *, H_Oe=0.0, sample_every=100, device=None, stream=None, engine=ENGINE_AUTO,
               dt=None):
     """The rod at level b (A(b), K(b) of Eqs. 8-9 for b > 1) at temperature T in a held field."""
     M = MAGNETITE

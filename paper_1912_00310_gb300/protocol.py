@@ -48,7 +48,7 @@ def level_grid(b: int):
 
 
 def make_grid(b: int, *, H_max=500.0, rate=2.5, dt=None, alpha=None, disp_deg=5.0, mode=2,
-              sample_dH=1.0, device=0, stream=None, engine=ENGINE_AUTO):
+              sample_dH=1.0, device=None, stream=None, engine=ENGINE_AUTO):
     M = MAGNETITE
     dims, volume = level_grid(b)
     g = Grid(*dims, a0=M["a0"], b=b, device=device, stream=stream)
@@ -121,7 +121,7 @@ def run_resumable(b: int, n_real: int, seed: int, checkpoint: str, *, max_second
     try:
         g.reset(seed=seed, n_real=n_real)
         total, every = g.steps_per_loop, g.sample_every
-        dev = torch.device("cuda", kw.get("device", 0))
+        dev = torch.device("cuda", g.device)
         S = torch.zeros((n_real, g.n_samples), dtype=torch.float32, device=dev)
         meta = json.dumps(dict(b=b, n_real=n_real, seed=seed, steps=total, n_samples=g.n_samples,
                                **{k: kw[k] for k in sorted(kw) if k != "device"}), sort_keys=True)

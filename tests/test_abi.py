@@ -207,3 +207,15 @@ def test_level_temperature_and_held_samples(pkg, orc):
     g.set_held_samples(21)
     assert g.n_samples == 21 and g.sample_every == 50
     g.close()
+
+
+def test_default_device_is_the_current_cuda_device(pkg, monkeypatch):
+    """A grid or peak measurement without an explicit device goes on the caller's current CUDA
+    device (one rank per GPU), and on device 0 without CUDA."""
+    import torch
+    import paper_1912_00310_gb300 as P
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: False)
+    assert P._current_device() == 0
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: True)
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 3)
+    assert P._current_device() == 3
