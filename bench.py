@@ -392,11 +392,17 @@ def side_measurements(args, torch, pkg, cfg, g, samples, S_per_step, flush):
 
     for _ in range(2):
         e2e_step()
+    _, world, _ = dist_env()
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         e2e_step()
     el = time.perf_counter() - t0
-    out["e2e"] = {"value": n_real * ncell * S_per_step * args.steps / el, "unit": UNIT,
+    # whole-job rate over all ranks: every rank's cell-steps over the slowest rank's time
+    e2e_value, _ = weak_scaling_value(el, n_real * ncell * S_per_step * args.steps,
+                                      device="cuda" if world > 1 else "cpu")
+    out["e2e"] = {"value": e2e_value, "unit": UNIT,
                   "h2d_bytes_per_step": m_host.numel() * 4,
                   "d2h_bytes_per_step": m_host.numel() * 4 + s_host.numel() * 4}
     # plain engine on the same b = 1 workload, bounded window
