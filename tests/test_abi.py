@@ -219,3 +219,28 @@ def test_default_device_is_the_current_cuda_device(pkg, monkeypatch):
     monkeypatch.setattr(torch.cuda, "is_available", lambda: True)
     monkeypatch.setattr(torch.cuda, "current_device", lambda: 3)
     assert P._current_device() == 3
+
+
+def test_tuning_keys_round_trip_and_ranges(pkg):
+    """Every tuning key reads back what was set, and each key's documented range is enforced
+    (EINVAL), on the host and without a GPU."""
+    g = _grid(pkg)
+    good = {pkg.TUNE_ROD_KIND: 3, pkg.TUNE_RODS_PER_CTA: 8, pkg.TUNE_CHUNK_STEPS: 4096,
+            pkg.TUNE_ROWS_PER_THREAD: 4, pkg.TUNE_GENERIC_KERNEL: 1, pkg.TUNE_BALANCE: 0,
+            pkg.TUNE_ADJOINT_STATE_MB: 1024, pkg.TUNE_CELLS_PER_THREAD: 2, pkg.TUNE_GRAD_METHOD: 1,
+            pkg.TUNE_HANDOFF_TIMEOUT_MS: 250, pkg.TUNE_WITHHOLD_HANDOFF: 1}
+    for key, value in good.items():
+        g.set_tuning(key, value)
+        assert g.tuning(key) == value, key
+    bad = [(pkg.TUNE_ROD_KIND, 4), (pkg.TUNE_ROWS_PER_THREAD, 5), (pkg.TUNE_CELLS_PER_THREAD, 3),
+           (pkg.TUNE_GRAD_METHOD, 2), (pkg.TUNE_HANDOFF_TIMEOUT_MS, 0),
+           (pkg.TUNE_HANDOFF_TIMEOUT_MS, 3600001), (pkg.TUNE_CHUNK_STEPS, (1 << 30) + 1),
+           (pkg.TUNE_ADJOINT_STATE_MB, (1 << 22) + 1), (pkg.TUNE_RODS_PER_CTA, 4097),
+           (pkg.TUNE_ROD_KIND, -1), (999, 1)]
+    for key, value in bad:
+        with pytest.raises(pkg.LLGError) as e:
+            g.set_tuning(key, value)
+        assert e.value.status == 1, (key, value)
+        if key in good:
+            assert g.tuning(key) == good[key]  # a refused value leaves the setting
+    g.close()
