@@ -157,8 +157,10 @@ extern "C" llg_status llg_loop_stats_host(const float *m_samples, int n_real, in
                                           double delta, llg_loop_stats *out, double *mean_out)
 {
     if (!m_samples || !H_Oe || !out || n_real < 1 || n_samples < 2 || k_turn < 1 ||
-        k_turn >= n_samples || mode < 0 || mode > 2)
+        k_turn >= n_samples || mode < 0 || mode > 2) {
+        llg::set_last_error("bad arguments to llg_loop_stats_host");
         return LLG_EINVAL;
+    }
     // the single-process case of the distributed reduction: sums, jackknife terms, statistics
     std::vector<double> sum((size_t)n_samples);
     llg_loop_moments(m_samples, n_real, n_samples, sum.data(), nullptr);

@@ -129,6 +129,14 @@ def test_loop_stats_match_oracle(pkg, orc):
     f = orc.m_rescale(2, 0.72902, 0.511)
     assert mine["area0_Oe"] == pytest.approx(ref["area"] * f / 0.72902, rel=1e-10)
     assert mine["Hc0_Oe"] == pytest.approx(ref["Hc"] / 0.72902, rel=1e-10)
+    # one realisation: that loop's own observables and no standard errors
+    one = pkg.loop_stats(S[:1], H, n_half, mode=1, zeta=1.0)
+    ref1 = orc.loop_stats(H, S[:1].astype(np.float64), n_half)
+    for key in ("Hc", "area", "Hc_down", "Hc_up"):
+        assert one[key + "_Oe"] == pytest.approx(ref1[key], rel=1e-10), key
+    assert np.isnan(one["Hc_se_Oe"]) and np.isnan(one["area_se_Oe"])
+    with pytest.raises(pkg.LLGError, match="llg_loop_stats_host"):
+        pkg.loop_stats(S, H, len(H), mode=1)  # the turning point past the last sample
 
 
 def test_gk_flow_matches_oracle(pkg, orc):
