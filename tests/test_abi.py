@@ -252,3 +252,16 @@ def test_tuning_keys_round_trip_and_ranges(pkg):
         if key in good:
             assert g.tuning(key) == good[key]  # a refused value leaves the setting
     g.close()
+
+
+def test_binding_constants_match_the_header():
+    """The binding's tuning keys, engines and status codes are the header's."""
+    from paper_1912_00310_gb300 import _lib
+    text = open(os.path.join(ROOT, "include", "llg.h")).read()
+    tune = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define LLG_TUNE_(\w+) (\d+)", text)}
+    assert tune and all(getattr(_lib, "TUNE_" + k) == v for k, v in tune.items()), tune
+    enums = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(LLG_\w+) = (\d+)", text)}
+    for name in ("AUTO", "RESIDENT", "PLAIN", "STREAM"):
+        assert getattr(_lib, "ENGINE_" + name) == enums["LLG_ENGINE_" + name]
+    for code, name in _lib.STATUS.items():
+        assert enums[name] == code, name
