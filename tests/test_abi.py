@@ -265,3 +265,17 @@ def test_binding_constants_match_the_header():
         assert getattr(_lib, "ENGINE_" + name) == enums["LLG_ENGINE_" + name]
     for code, name in _lib.STATUS.items():
         assert enums[name] == code, name
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    """Every prototype of the header has a ctypes signature in the binding with the same number of
+    arguments, and the binding declares nothing the header does not."""
+    from paper_1912_00310_gb300 import _lib
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "llg.h")).read(), flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b(llg_\w+)\s*\(([^;{]*?)\)\s*;", text):
+        args = m.group(2).strip()
+        protos[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    assert set(protos) == set(_lib.SIGNATURES), set(protos) ^ set(_lib.SIGNATURES)
+    for name, (_, argtypes) in _lib.SIGNATURES.items():
+        assert len(argtypes) == protos[name], name
